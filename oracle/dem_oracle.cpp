@@ -1,0 +1,616 @@
+// FP64 reference oracle for the soft-sphere DEM timestep (TEST INFRASTRUCTURE).
+//
+// This file is test infrastructure, not part of the product path.  Only the
+// tests, the smoke check and the CPU-baseline leg of the benchmark load it.
+// It shares no code, header, helper or constant with the CUDA library.
+//
+// It is a plain, slow, literal restatement of the method of arXiv 2507.12610
+// ("TinyDEM"), Sec. 2 (particle model) and Sec. 3.2-3.3 (contact bookkeeping),
+// in double precision with O(N^2) particle-pair search and O(N*M)
+// particle-triangle search.  No cells, no lists, no blocking, no reordering.
+//
+// Readings of the paper taken here (each one is listed with its reason in the
+// design notes of the repository):
+//   * Contact-point velocity, Sec. 2.2: the rotational term is taken as
+//     n x (r_i w_i + r_j w_j).  The printed minus sign contradicts the contact
+//     point kinematics and the sliding-torque relation of Sec. 3.2; the literal
+//     sign is available behind `literal_sign` so tests can show the difference.
+//   * Degenerate projection of a friction spring (Sec. 2.3): if the spring or
+//     its tangential part has zero length, the spring becomes zero.
+//   * Coulomb test is inclusive (|f| <= mu |f_n| is static).  Kinetic twisting
+//     sets f_t = mu_t |f_n| sign(f_t).
+//   * Contact lifetime (Sec. 3.2): a contact exists in a step iff delta >= 0; its
+//     history starts at zero and is dropped on the first step with delta < 0.
+//   * Mesh elements (Sec. 2.2, 3.3): R_j = E_j = m_j = infinity, so R* = R_i,
+//     m* = m_i; the element radius enters only delta.  Each touching triangle is
+//     an independent contact (ghost collisions are kept, Sec. 3.3).
+//   * Rotating mesh (not in the paper, which keeps walls static): the mesh turns
+//     rigidly with angular velocity Omega about `mesh_center`; at step n its
+//     vertices are the reference vertices rotated by angle |Omega| n dt.  The
+//     wall velocity at the contact point x_c = x_i - r_i n is Omega x (x_c - c),
+//     and the wall's angular velocity in the rolling/twisting terms is Omega.
+//   * Summation order: contributions to a particle are added in ascending
+//     partner index, then ascending triangle index (single-evaluation loop
+//     over i < j, Sec. 3.2, followed by the mesh loop).
+//
+// Build: g++ -O2 -ffp-contract=off -fPIC -shared (no fused multiply-add
+// contraction, so the oracle gives the same bits on x86-64 and aarch64).
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <map>
+#include <utility>
+#include <vector>
+
+namespace {
+
+struct V3 {
+  double x, y, z;
+};
+inline V3 v3(double x, double y, double z) { return V3{x, y, z}; }
+inline V3 operator+(V3 a, V3 b) { return v3(a.x + b.x, a.y + b.y, a.z + b.z); }
+inline V3 operator-(V3 a, V3 b) { return v3(a.x - b.x, a.y - b.y, a.z - b.z); }
+inline V3 operator-(V3 a) { return v3(-a.x, -a.y, -a.z); }
+inline V3 operator*(double s, V3 a) { return v3(s * a.x, s * a.y, s * a.z); }
+inline double dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+inline V3 cross(V3 a, V3 b) {
+  return v3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+inline double norm(V3 a) { return std::sqrt(dot(a, a)); }
+inline V3 load3(const double* p, int64_t i) { return v3(p[3 * i], p[3 * i + 1], p[3 * i + 2]); }
+inline void store3(double* p, int64_t i, V3 a) {
+  p[3 * i] = a.x;
+  p[3 * i + 1] = a.y;
+  p[3 * i + 2] = a.z;
+}
+
+}  // namespace
+
+extern "C" {
+
+// Layout must match oracle/oracle.py (ctypes).
+struct oracle_params {
+  double E, nu, rho, e_n, mu_s, mu_r, mu_t, eta;
+  double g[3];
+  double dt;
+  double mesh_omega[3];
+  double mesh_center[3];
+  int32_t literal_sign;  // 1: use the printed minus sign in the contact velocity
+  int32_t reserved;
+};
+
+}  // extern "C"
+
+namespace {
+
+// Static friction history of one contact (Table 3): u_s, u_r, u_t.
+struct Hist {
+  V3 us{0, 0, 0};
+  V3 ur{0, 0, 0};
+  double ut = 0;
+};
+
+// Contact key (Sec. 3.2): (i, j) with i < j for particle pairs; mesh element k
+// is labelled by the non-positive index j = -1 - k.
+using Key = std::pair<int64_t, int64_t>;
+
+struct Scene {
+  oracle_params p;
+  int64_t n = 0;
+  std::vector<double> R, x, v, w, q;  // R[n], x/v/w[3n], q[4n] (scalar first)
+  std::vector<double> F, T;           // contact force / torque sums of the last step
+  int64_t nv = 0, nt = 0;
+  std::vector<double> vert0;          // reference vertices [3 nv]
+  std::vector<int32_t> tri;           // [3 nt]
+  std::vector<double> tri_radius;     // [nt]
+  std::map<Key, Hist> hist;
+  int64_t step_count = 0;
+  int64_t degenerate = 0;  // contacts skipped because d == 0
+};
+
+// Damping factor beta(e_n) of Sec. 2.2.
+double beta_of(double e_n) {
+  if (e_n <= 0.0) return 1.0;  // ln e_n -> -inf
+  if (e_n >= 1.0) return 0.0;  // ln e_n -> 0
+  const double l = std::log(e_n);
+  const double r = M_PI / l;
+  return 1.0 / std::sqrt(1.0 + r * r);
+}
+
+// Closest point on triangle (a, b, c) to point p: the minimiser of |p - y| over
+// the triangle, written out directly.  If the projection of p onto the plane
+// lies inside the triangle (all barycentric coordinates >= 0) it is the answer;
+// otherwise the minimiser lies on the boundary, i.e. on one of the three edges,
+// each of which is handled as a clamped segment projection.
+V3 closest_on_segment(V3 p, V3 a, V3 b) {
+  V3 ab = b - a;
+  double L2 = dot(ab, ab);
+  if (L2 <= 0.0) return a;
+  double t = dot(p - a, ab) / L2;
+  if (t < 0.0) t = 0.0;
+  if (t > 1.0) t = 1.0;
+  return a + t * ab;
+}
+
+V3 closest_on_triangle(V3 p, V3 a, V3 b, V3 c) {
+  V3 ab = b - a, ac = c - a;
+  V3 nrm = cross(ab, ac);
+  double n2 = dot(nrm, nrm);
+  if (n2 > 0.0) {
+    // projection onto the plane and its barycentric coordinates
+    double s = dot(p - a, nrm) / n2;
+    V3 y = p - s * nrm;
+    // barycentric weights via sub-triangle areas (signed, along nrm)
+    double wa = dot(cross(b - y, c - y), nrm) / n2;
+    double wb = dot(cross(c - y, a - y), nrm) / n2;
+    double wc = dot(cross(a - y, b - y), nrm) / n2;
+    if (wa >= 0.0 && wb >= 0.0 && wc >= 0.0) return y;
+  }
+  V3 c1 = closest_on_segment(p, a, b);
+  V3 c2 = closest_on_segment(p, b, c);
+  V3 c3 = closest_on_segment(p, c, a);
+  double d1 = dot(p - c1, p - c1), d2 = dot(p - c2, p - c2), d3 = dot(p - c3, p - c3);
+  V3 best = c1;
+  double bd = d1;
+  if (d2 < bd) { best = c2; bd = d2; }
+  if (d3 < bd) { best = c3; bd = d3; }
+  return best;
+}
+
+// Rodrigues rotation of vector r by angle th about unit axis k.
+V3 rotate(V3 r, V3 k, double th) {
+  double c = std::cos(th), s = std::sin(th);
+  return c * r + s * cross(k, r) + (dot(k, r) * (1.0 - c)) * k;
+}
+
+// Friction spring of mode m in {s, r} (Sec. 2.3): project the stored spring
+// onto the current tangent plane and restore its length, evaluate
+// f = -k u - c v, then apply the Coulomb limit mu |f_n| and update u.
+V3 friction_vec(V3& u, V3 n, V3 vm, double k, double c, double mu, double fn_mag, double dt) {
+  // projection back onto the tangent plane, length preserved (zero if degenerate)
+  double ulen = norm(u);
+  V3 ut = u - dot(u, n) * n;
+  double utlen = norm(ut);
+  if (ulen > 0.0 && utlen > 0.0)
+    u = (ulen / utlen) * ut;
+  else
+    u = v3(0, 0, 0);
+  V3 f = -k * u - c * vm;
+  double flen = norm(f);
+  if (flen <= mu * fn_mag) {
+    u = u + dt * vm;  // static regime
+  } else {
+    f = (mu * fn_mag / flen) * f;   // kinetic regime: clip to the Coulomb bound
+    u = (-1.0 / k) * (f + c * vm);  // spring set to satisfy Coulomb exactly
+  }
+  return f;
+}
+
+double friction_scalar(double& u, double vm, double k, double c, double mu, double fn_mag, double dt) {
+  double f = -k * u - c * vm;
+  if (std::fabs(f) <= mu * fn_mag) {
+    u = u + dt * vm;
+  } else {
+    f = (f > 0.0 ? 1.0 : -1.0) * mu * fn_mag;
+    u = (-1.0 / k) * (f + c * vm);
+  }
+  return f;
+}
+
+struct Coeffs {
+  double Es, Gs, Rs, ms;  // effective modulus, shear modulus, radius, mass
+  double kn, ks, cn, cs;  // stiffness and damping coefficients
+};
+
+// Effective properties and contact coefficients (Sec. 2.2).  All particles
+// share E, nu, rho; a wall has E_j = G_j = R_j = m_j = infinity, so the terms
+// with 1/inf vanish.
+Coeffs contact_coeffs(const oracle_params& p, bool wall, double Ri, double mi, double Rj,
+                      double mj, double delta) {
+  const double E = p.E, nu = p.nu;
+  const double G = E / (2.0 * (1.0 + nu));
+  Coeffs k;
+  if (wall) {
+    k.Es = 1.0 / ((1.0 - nu * nu) / E);
+    k.Gs = 1.0 / ((2.0 - nu) / G);
+    k.Rs = Ri;
+    k.ms = mi;
+  } else {
+    k.Es = 1.0 / ((1.0 - nu * nu) / E + (1.0 - nu * nu) / E);
+    k.Gs = 1.0 / ((2.0 - nu) / G + (2.0 - nu) / G);
+    k.Rs = 1.0 / (1.0 / Ri + 1.0 / Rj);
+    k.ms = 1.0 / (1.0 / mi + 1.0 / mj);
+  }
+  const double a = std::sqrt(k.Rs * delta);  // contact radius
+  k.kn = 4.0 / 3.0 * k.Es * a;
+  k.ks = 8.0 * k.Gs * a;
+  const double beta = beta_of(p.e_n);
+  k.cn = std::sqrt(5.0 * k.ms * k.kn) * beta;
+  k.cs = std::sqrt(k.ms * k.ks / 6.0) * beta;
+  return k;
+}
+
+struct ContactOut {
+  V3 f;      // force on i (f_n + f_s)
+  V3 tau_i;  // torque on i (tau_s + tau_r + tau_t)
+  V3 tau_j;  // torque on j (r_j f_s x n - tau_r - tau_t); unused for walls
+};
+
+// The inelastic Hertz-Mindlin contact law with sliding, rolling and twisting
+// friction (Sec. 2.2) and the history update of Sec. 2.3, for body i against
+// body j.  For a wall, j is infinitely large, stiff and heavy; its surface
+// velocity at the contact point and its angular velocity are given directly.
+ContactOut contact_law(const oracle_params& p, V3 nhat, double delta,
+                       double Ri, double mi, V3 vi, V3 wi,
+                       bool wall, double Rj, double mj, V3 vj, V3 wj, V3 vwall,
+                       Hist& h, bool literal_sign) {
+  const Coeffs k = contact_coeffs(p, wall, Ri, mi, Rj, mj, delta);
+  const double Rs = k.Rs;
+  const double kn = k.kn, ks = k.ks, cn = k.cn, cs = k.cs;
+  const double kr = kn, cr = cn, kt = ks, ct = cs;
+  // distances from the centres to the contact point
+  const double ri = Ri - delta / 2.0;
+  const double rj = wall ? INFINITY : Rj - delta / 2.0;
+  // relative velocity at the contact point and its decomposition
+  V3 v;
+  if (wall) {
+    v = vi - vwall + cross(nhat, ri * wi);
+  } else {
+    V3 rot = literal_sign ? (ri * wi - rj * wj) : (ri * wi + rj * wj);
+    v = vi - vj + cross(nhat, rot);
+  }
+  const V3 vn = dot(v, nhat) * nhat;
+  const V3 vs = v - vn;
+  const V3 om = wi - wj;
+  const double inv_r = wall ? 1.0 / ri : 1.0 / ri + 1.0 / rj;
+  const V3 vr = (1.0 / inv_r) * cross(om, nhat);
+  const double vt = Rs * dot(om, nhat);
+  // normal force
+  const V3 un = -delta * nhat;
+  const V3 fn = -kn * un - cn * vn;
+  const double fn_mag = norm(fn);
+  // friction modes, each independently static or kinetic
+  const V3 fs = friction_vec(h.us, nhat, vs, ks, cs, p.mu_s, fn_mag, p.dt);
+  const V3 fr = friction_vec(h.ur, nhat, vr, kr, cr, p.mu_r, fn_mag, p.dt);
+  const double ft = friction_scalar(h.ut, vt, kt, ct, p.mu_t, fn_mag, p.dt);
+  // torques
+  const V3 tau_s = ri * cross(fs, nhat);
+  const V3 tau_r = Rs * cross(nhat, fr);
+  const V3 tau_t = (ft * Rs) * nhat;
+  ContactOut o;
+  o.f = fn + fs;
+  o.tau_i = tau_s + tau_r + tau_t;
+  if (!wall) o.tau_j = rj * cross(fs, nhat) - tau_r - tau_t;  // Eqs. antisymm_*
+  else o.tau_j = v3(0, 0, 0);
+  return o;
+}
+
+double mass_of(const oracle_params& p, double R) { return 4.0 / 3.0 * M_PI * p.rho * R * R * R; }
+
+// Hamilton product (Sec. 2.3).
+void qmul(const double* a, const double* b, double* out) {
+  double s = a[0] * b[0] - (a[1] * b[1] + a[2] * b[2] + a[3] * b[3]);
+  V3 av = v3(a[1], a[2], a[3]), bv = v3(b[1], b[2], b[3]);
+  V3 r = a[0] * bv + b[0] * av + cross(av, bv);
+  out[0] = s;
+  out[1] = r.x;
+  out[2] = r.y;
+  out[3] = r.z;
+}
+
+// Semi-implicit Euler step of one particle (Sec. 2.3): accelerations from the
+// contact sums, gravity and Stokes drag; v then x (with the new v); the SPIRAL
+// orientation update with the angular velocity before its update; then w.
+void integrate_particle(const oracle_params& p, double R, V3 F, V3 T, V3& x, V3& v, V3& w,
+                        double* q) {
+  const double m = mass_of(p, R);
+  const double I = 2.0 / 5.0 * m * R * R;
+  const double ci = 9.0 * p.eta / (2.0 * p.rho * R * R);  // Stokes drag rates
+  const double gi = 10.0 / 3.0 * ci;
+  const V3 g = load3(p.g, 0);
+  const V3 a = (1.0 / m) * F + g - ci * v;
+  const V3 al = (1.0 / I) * T - gi * w;
+  v = v + p.dt * a;
+  x = x + p.dt * v;
+  // q <- q (cos phi, sin phi w/|w|) (cos theta, sin theta al/|al|), each
+  // product only if the rotation vector is non-zero
+  const double wn = norm(w);
+  if (wn > 0.0) {
+    const double phi = p.dt / 2.0 * wn;
+    const double r[4] = {std::cos(phi), std::sin(phi) * w.x / wn, std::sin(phi) * w.y / wn,
+                         std::sin(phi) * w.z / wn};
+    double t[4];
+    qmul(q, r, t);
+    std::memcpy(q, t, sizeof t);
+  }
+  const double an = norm(al);
+  if (an > 0.0) {
+    const double th = (p.dt / 2.0) * (p.dt / 2.0) * an;
+    const double r[4] = {std::cos(th), std::sin(th) * al.x / an, std::sin(th) * al.y / an,
+                         std::sin(th) * al.z / an};
+    double t[4];
+    qmul(q, r, t);
+    std::memcpy(q, t, sizeof t);
+  }
+  w = w + p.dt * al;
+}
+
+V3 mesh_vertex(const Scene& S, int64_t k) {
+  V3 r0 = load3(S.vert0.data(), k);
+  V3 Om = load3(S.p.mesh_omega, 0);
+  double wm = norm(Om);
+  if (!(wm > 0.0)) return r0;
+  V3 c = load3(S.p.mesh_center, 0);
+  double th = wm * ((double)S.step_count * S.p.dt);
+  return c + rotate(r0 - c, (1.0 / wm) * Om, th);
+}
+
+// One timestep: contact search and forces at t_n, then integration to t_{n+1}.
+void step_once(Scene& S) {
+  const oracle_params& p = S.p;
+  const int64_t n = S.n;
+  std::fill(S.F.begin(), S.F.end(), 0.0);
+  std::fill(S.T.begin(), S.T.end(), 0.0);
+  std::map<Key, Hist> next;
+
+  // particle-particle contacts, each unordered pair evaluated once (i < j)
+  for (int64_t i = 0; i < n; ++i) {
+    const V3 xi = load3(S.x.data(), i), vi = load3(S.v.data(), i), wi = load3(S.w.data(), i);
+    const double Ri = S.R[i], mi = mass_of(p, Ri);
+    for (int64_t j = i + 1; j < n; ++j) {
+      const V3 xj = load3(S.x.data(), j);
+      const V3 d = xi - xj;
+      const double dist = norm(d);
+      const double delta = Ri + S.R[j] - dist;
+      if (delta < 0.0) continue;  // not touching: any history is dropped
+      if (!(dist > 0.0)) { ++S.degenerate; continue; }
+      const V3 nhat = (1.0 / dist) * d;
+      Hist h;
+      auto it = S.hist.find(Key(i, j));
+      if (it != S.hist.end()) h = it->second;
+      const double Rj = S.R[j];
+      ContactOut o = contact_law(p, nhat, delta, Ri, mi, vi, wi, false, Rj, mass_of(p, Rj),
+                                 load3(S.v.data(), j), load3(S.w.data(), j), v3(0, 0, 0), h,
+                                 p.literal_sign != 0);
+      store3(S.F.data(), i, load3(S.F.data(), i) + o.f);
+      store3(S.F.data(), j, load3(S.F.data(), j) - o.f);
+      store3(S.T.data(), i, load3(S.T.data(), i) + o.tau_i);
+      store3(S.T.data(), j, load3(S.T.data(), j) + o.tau_j);
+      next[Key(i, j)] = h;
+    }
+  }
+
+  // particle-triangle contacts
+  if (S.nt > 0) {
+    std::vector<V3> vt(S.nv);
+    for (int64_t k = 0; k < S.nv; ++k) vt[k] = mesh_vertex(S, k);
+    const V3 Om = load3(p.mesh_omega, 0), c = load3(p.mesh_center, 0);
+    for (int64_t i = 0; i < n; ++i) {
+      const V3 xi = load3(S.x.data(), i), vi = load3(S.v.data(), i), wi = load3(S.w.data(), i);
+      const double Ri = S.R[i], mi = mass_of(p, Ri);
+      for (int64_t k = 0; k < S.nt; ++k) {
+        const V3 pc = closest_on_triangle(xi, vt[S.tri[3 * k]], vt[S.tri[3 * k + 1]],
+                                          vt[S.tri[3 * k + 2]]);
+        const V3 d = xi - pc;
+        const double dist = norm(d);
+        const double delta = Ri + S.tri_radius[k] - dist;
+        if (delta < 0.0) continue;
+        if (!(dist > 0.0)) { ++S.degenerate; continue; }
+        const V3 nhat = (1.0 / dist) * d;
+        Hist h;
+        const Key key(i, -1 - k);
+        auto it = S.hist.find(key);
+        if (it != S.hist.end()) h = it->second;
+        const double ri = Ri - delta / 2.0;
+        const V3 xc = xi - ri * nhat;  // contact point
+        const V3 vwall = cross(Om, xc - c);
+        ContactOut o = contact_law(p, nhat, delta, Ri, mi, vi, wi, true, INFINITY, INFINITY,
+                                   v3(0, 0, 0), Om, vwall, h, false);
+        store3(S.F.data(), i, load3(S.F.data(), i) + o.f);
+        store3(S.T.data(), i, load3(S.T.data(), i) + o.tau_i);
+        next[key] = h;
+      }
+    }
+  }
+  S.hist.swap(next);
+
+  // semi-implicit Euler with the SPIRAL quaternion update (Sec. 2.3)
+  for (int64_t i = 0; i < n; ++i) {
+    V3 x = load3(S.x.data(), i), v = load3(S.v.data(), i), w = load3(S.w.data(), i);
+    integrate_particle(p, S.R[i], load3(S.F.data(), i), load3(S.T.data(), i), x, v, w, &S.q[4 * i]);
+    store3(S.v.data(), i, v);
+    store3(S.x.data(), i, x);
+    store3(S.w.data(), i, w);
+  }
+  S.step_count += 1;
+}
+
+}  // namespace
+
+extern "C" {
+
+void* oracle_create(const oracle_params* p, int64_t n, const double* R, const double* x,
+                    const double* v, const double* w, const double* q, int64_t nv,
+                    const double* vert, int64_t nt, const int32_t* tri, const double* tri_radius) {
+  Scene* S = new Scene();
+  S->p = *p;
+  S->n = n;
+  S->R.assign(R, R + n);
+  S->x.assign(x, x + 3 * n);
+  S->v.assign(v, v + 3 * n);
+  S->w.assign(w, w + 3 * n);
+  S->q.assign(q, q + 4 * n);
+  S->F.assign(3 * n, 0.0);
+  S->T.assign(3 * n, 0.0);
+  S->nv = nv;
+  S->nt = nt;
+  if (nv > 0) S->vert0.assign(vert, vert + 3 * nv);
+  if (nt > 0) {
+    S->tri.assign(tri, tri + 3 * nt);
+    S->tri_radius.assign(tri_radius, tri_radius + nt);
+  }
+  return S;
+}
+
+void oracle_destroy(void* s) { delete static_cast<Scene*>(s); }
+
+void oracle_step(void* s, int64_t nsteps) {
+  Scene* S = static_cast<Scene*>(s);
+  for (int64_t k = 0; k < nsteps; ++k) step_once(*S);
+}
+
+void oracle_read_state(void* s, double* x, double* v, double* w, double* q) {
+  Scene* S = static_cast<Scene*>(s);
+  std::memcpy(x, S->x.data(), sizeof(double) * 3 * S->n);
+  std::memcpy(v, S->v.data(), sizeof(double) * 3 * S->n);
+  std::memcpy(w, S->w.data(), sizeof(double) * 3 * S->n);
+  std::memcpy(q, S->q.data(), sizeof(double) * 4 * S->n);
+}
+
+void oracle_read_forces(void* s, double* F, double* T) {
+  Scene* S = static_cast<Scene*>(s);
+  std::memcpy(F, S->F.data(), sizeof(double) * 3 * S->n);
+  std::memcpy(T, S->T.data(), sizeof(double) * 3 * S->n);
+}
+
+int64_t oracle_num_contacts(void* s) { return (int64_t) static_cast<Scene*>(s)->hist.size(); }
+int64_t oracle_degenerate(void* s) { return static_cast<Scene*>(s)->degenerate; }
+int64_t oracle_step_count(void* s) { return static_cast<Scene*>(s)->step_count; }
+
+// Contacts in key order: keys[2k] = i, keys[2k+1] = j (j < 0: triangle -1-j);
+// hist[7k..7k+6] = u_s, u_r, u_t.
+void oracle_read_contacts(void* s, int64_t* keys, double* hist) {
+  Scene* S = static_cast<Scene*>(s);
+  int64_t k = 0;
+  for (const auto& kv : S->hist) {
+    keys[2 * k] = kv.first.first;
+    keys[2 * k + 1] = kv.first.second;
+    const Hist& h = kv.second;
+    double* o = hist + 7 * k;
+    o[0] = h.us.x; o[1] = h.us.y; o[2] = h.us.z;
+    o[3] = h.ur.x; o[4] = h.ur.y; o[5] = h.ur.z;
+    o[6] = h.ut;
+    ++k;
+  }
+}
+
+// Replace the contact history (keys / hist in the layout of oracle_read_contacts).
+void oracle_set_contacts(void* s, int64_t m, const int64_t* keys, const double* hist) {
+  Scene* S = static_cast<Scene*>(s);
+  S->hist.clear();
+  for (int64_t k = 0; k < m; ++k) {
+    Hist h;
+    const double* o = hist + 7 * k;
+    h.us = v3(o[0], o[1], o[2]);
+    h.ur = v3(o[3], o[4], o[5]);
+    h.ut = o[6];
+    S->hist[Key(keys[2 * k], keys[2 * k + 1])] = h;
+  }
+}
+
+void oracle_set_step_count(void* s, int64_t c) { static_cast<Scene*>(s)->step_count = c; }
+
+// Closest point on a triangle, exposed for tests.
+void oracle_closest_on_triangle(const double* p, const double* a, const double* b,
+                                const double* c, double* out) {
+  V3 r = closest_on_triangle(load3(p, 0), load3(a, 0), load3(b, 0), load3(c, 0));
+  store3(out, 0, r);
+}
+
+double oracle_beta(double e_n) { return beta_of(e_n); }
+
+// Contact coefficients for tests: out = {E*, G*, R*, m*, k_n, k_s, c_n, c_s}.
+// For a wall (wall != 0) Rj is ignored.
+void oracle_contact_coeffs(const oracle_params* p, int32_t wall, double Ri, double Rj,
+                           double delta, double* out) {
+  const double mi = mass_of(*p, Ri);
+  const double mj = wall ? INFINITY : mass_of(*p, Rj);
+  Coeffs k = contact_coeffs(*p, wall != 0, Ri, mi, wall ? INFINITY : Rj, mj, delta);
+  const double v[8] = {k.Es, k.Gs, k.Rs, k.ms, k.kn, k.ks, k.cn, k.cs};
+  std::memcpy(out, v, sizeof v);
+}
+
+// One step for a sample of particles, evaluated one by one from a state with
+// no contact history (the first step of a run): for each sampled particle the
+// contact sums over all other particles (ascending index) and all triangles
+// (ascending index), then the integrated state.  Used to check large runs on
+// a subset of outputs.  Output rows follow `ids`.
+void oracle_sample_first_step(const oracle_params* p, int64_t n, const double* R, const double* x,
+                              const double* v, const double* w, const double* q, int64_t nv,
+                              const double* vert, int64_t nt, const int32_t* tri,
+                              const double* tri_radius, int64_t step_index, int64_t ns,
+                              const int64_t* ids, double* F_out, double* T_out, double* x_out,
+                              double* v_out, double* w_out, double* q_out) {
+  // Build a scene holding only what is needed: all particles (to find
+  // partners) but integrate only the sampled ones.
+  Scene S;
+  S.p = *p;
+  S.n = n;
+  S.nv = nv;
+  S.nt = nt;
+  S.step_count = step_index;
+  if (nv > 0) S.vert0.assign(vert, vert + 3 * nv);
+  if (nt > 0) {
+    S.tri.assign(tri, tri + 3 * nt);
+    S.tri_radius.assign(tri_radius, tri_radius + nt);
+  }
+  std::vector<V3> vt(nv);
+  for (int64_t k = 0; k < nv; ++k) vt[k] = mesh_vertex(S, k);
+  const V3 Om = load3(p->mesh_omega, 0), c = load3(p->mesh_center, 0);
+  for (int64_t s = 0; s < ns; ++s) {
+    const int64_t i = ids[s];
+    const V3 xi = load3(x, i), vi = load3(v, i), wi = load3(w, i);
+    const double Ri = R[i], mi = mass_of(*p, Ri);
+    V3 F = v3(0, 0, 0), T = v3(0, 0, 0);
+    for (int64_t j = 0; j < n; ++j) {
+      if (j == i) continue;
+      // evaluate the pair in canonical order (lower index first), as the
+      // single-evaluation loop does, and take i's side
+      const int64_t lo = i < j ? i : j, hi = i < j ? j : i;
+      const V3 d = load3(x, lo) - load3(x, hi);
+      const double dist = norm(d);
+      const double delta = R[lo] + R[hi] - dist;
+      if (delta < 0.0 || !(dist > 0.0)) continue;
+      const V3 nhat = (1.0 / dist) * d;
+      Hist h;
+      ContactOut o = contact_law(*p, nhat, delta, R[lo], mass_of(*p, R[lo]), load3(v, lo),
+                                 load3(w, lo), false, R[hi], mass_of(*p, R[hi]), load3(v, hi),
+                                 load3(w, hi), v3(0, 0, 0), h, p->literal_sign != 0);
+      if (i == lo) {
+        F = F + o.f;
+        T = T + o.tau_i;
+      } else {
+        F = F - o.f;
+        T = T + o.tau_j;
+      }
+    }
+    for (int64_t k = 0; k < nt; ++k) {
+      const V3 pc = closest_on_triangle(xi, vt[tri[3 * k]], vt[tri[3 * k + 1]], vt[tri[3 * k + 2]]);
+      const V3 d = xi - pc;
+      const double dist = norm(d);
+      const double delta = Ri + tri_radius[k] - dist;
+      if (delta < 0.0 || !(dist > 0.0)) continue;
+      const V3 nhat = (1.0 / dist) * d;
+      Hist h;
+      const double ri = Ri - delta / 2.0;
+      const V3 xc = xi - ri * nhat;
+      ContactOut o = contact_law(*p, nhat, delta, Ri, mi, vi, wi, true, INFINITY, INFINITY,
+                                 v3(0, 0, 0), Om, cross(Om, xc - c), h, false);
+      F = F + o.f;
+      T = T + o.tau_i;
+    }
+    store3(F_out, s, F);
+    store3(T_out, s, T);
+    // integrate this particle alone (same update as a full step)
+    V3 xx = xi, vv = vi, ww = wi;
+    double qq[4] = {q[4 * i], q[4 * i + 1], q[4 * i + 2], q[4 * i + 3]};
+    integrate_particle(*p, Ri, F, T, xx, vv, ww, qq);
+    store3(x_out, s, xx);
+    store3(v_out, s, vv);
+    store3(w_out, s, ww);
+    std::memcpy(q_out + 4 * s, qq, sizeof qq);
+  }
+}
+
+}  // extern "C"
