@@ -1,0 +1,177 @@
+/*
+ * dem.h -- C ABI of the GB300 soft-sphere DEM timestep library (libdem.so).
+ *
+ * The library advances a 3D ensemble of frictional spheres and a rigid
+ * triangle mesh with the method of arXiv 2507.12610 ("TinyDEM"):
+ *   - damped Newton-Euler equations of motion with Stokes drag (Sec. 2.1,
+ *     Eqs. translation / rotation),
+ *   - the visco-elastic Hertz-Mindlin contact law with Coulomb-limited
+ *     sliding, rolling and twisting springs whose history persists for the
+ *     life of a contact (Sec. 2.2, Eqs. fn, fs, fr, ft, Coulombs/r/t; Sec. 2.3,
+ *     Eqs. um, um_static, fm_kinetic, um_kinetic),
+ *   - sphere-triangle mesh contacts with the wall limits R_j = E_j = m_j = inf
+ *     (Sec. 2.2) and one independent contact per touching element (Sec. 3.3),
+ *   - semi-implicit Euler integration with the synchronous SPIRAL quaternion
+ *     update (Sec. 2.3, Eqs. v, x, w, spiral).
+ * Contact search uses cell binning and a Verlet list with skin, the extension
+ * suggested in Sec. 7; results do not depend on the skin or rebuild schedule.
+ *
+ * Conventions for every entry point:
+ *   - Host arrays are borrowed for the duration of the call only; the
+ *     library owns all device memory it allocates.
+ *   - Vectors are row-major [n][3] doubles; quaternions [n][4] doubles with
+ *     the scalar part first.  State is always exchanged in the caller's
+ *     particle order (index 0..n-1), whatever order the device uses.
+ *   - Every call returns a status code (DEM_OK = 0) and never throws.  Device
+ *     errors are sticky: once a step fails, later steps do no work and
+ *     dem_synchronize() reports the first error.
+ *   - A scene is bound to the CUDA device current at creation and to one
+ *     stream; calls on one scene must not run concurrently.
+ */
+#ifndef DEM_H_
+#define DEM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define DEM_OK 0
+#define DEM_ERR_INVALID 1   /* argument violates the requirements of Table 2 or the layout */
+#define DEM_ERR_CAPACITY 2  /* a neighbour or mesh-contact list overflowed its capacity */
+#define DEM_ERR_NONFINITE 3 /* a particle state became NaN or infinite */
+#define DEM_ERR_TIMEOUT 4   /* a bounded device wait gave up */
+#define DEM_ERR_CUDA 5      /* a CUDA runtime call failed */
+#define DEM_ERR_NOMEM 6     /* device memory allocation failed */
+
+/* precision of the contact arithmetic */
+#define DEM_FP64 0  /* everything in IEEE double precision */
+#define DEM_MIXED 1 /* contact geometry, forces and springs in FP32; positions,
+                       velocities, spins and orientations integrated as
+                       compensated double-float pairs (two FP32 words, ~48-bit
+                       significand); forces summed with compensated FP32 */
+
+/* Material, kinetic and numerical parameters.  Physical parameters follow
+ * Table 2 of the paper and must satisfy its "Requirements" column:
+ * E > 0, nu in (-1, 0.5], rho > 0, e_n in [0, 1], mu_* >= 0, eta >= 0, dt > 0. */
+typedef struct dem_params {
+  double E;        /* Young's modulus (Pa) */
+  double nu;       /* Poisson's ratio */
+  double rho;      /* mass density (kg/m^3), shared by all particles */
+  double e_n;      /* coefficient of normal restitution */
+  double mu_s;     /* sliding friction coefficient */
+  double mu_r;     /* rolling friction coefficient */
+  double mu_t;     /* twisting friction coefficient */
+  double eta;      /* dynamic viscosity of the Stokes drag (Pa s) */
+  double g[3];     /* external acceleration (m/s^2) */
+  double dt;       /* time step (s) */
+  double mesh_omega[3];  /* angular velocity of the rigid mesh (rad/s); the mesh
+                            is the reference mesh rotated by |omega| t about the
+                            axis through mesh_center (extension: the paper's
+                            walls are static) */
+  double mesh_center[3]; /* point on the rotation axis (m) */
+  double skin;           /* Verlet skin (m); <= 0 selects 0.25 R_max */
+  double domain_lo[3];   /* binning box (m); if any lo >= hi the box is the */
+  double domain_hi[3];   /*   bounding box of particles and mesh, padded     */
+  int32_t precision;     /* DEM_FP64 or DEM_MIXED */
+  int32_t max_neighbors; /* list capacity per particle; <= 0 selects 64 */
+  int32_t max_mesh_contacts; /* triangle-candidate capacity per particle; <= 0: 16 */
+  int32_t record_forces; /* nonzero: keep per-particle contact sums for dem_read_forces */
+} dem_params;
+
+/* Particles (host arrays, caller order). */
+typedef struct dem_particles {
+  int64_t n;         /* number of particles, >= 1 */
+  const double* R;   /* [n] radii, > 0 */
+  const double* x;   /* [n][3] positions */
+  const double* v;   /* [n][3] velocities; NULL = zero */
+  const double* w;   /* [n][3] angular velocities; NULL = zero */
+  const double* q;   /* [n][4] unit quaternions (scalar first); NULL = identity */
+} dem_particles;
+
+/* Rigid triangle mesh in its reference pose (host arrays); may be empty. */
+typedef struct dem_mesh {
+  int64_t n_vert;
+  const double* vert;        /* [n_vert][3] */
+  int64_t n_tri;
+  const int32_t* tri;        /* [n_tri][3] vertex indices in [0, n_vert) */
+  const double* tri_radius;  /* [n_tri] element radius R_j >= 0 (Sec. 3.3); NULL = 0 */
+} dem_mesh;
+
+typedef struct dem_stats {
+  int64_t steps;          /* steps completed */
+  int64_t rebuilds;       /* neighbour-list rebuilds performed */
+  int64_t pair_contacts;  /* touching particle pairs in the last step */
+  int64_t mesh_contacts;  /* touching particle-triangle pairs in the last step */
+  int64_t list_entries;   /* directed candidate entries in the current list */
+  int64_t mesh_candidates;/* particle-triangle candidates in the current list */
+  int32_t max_list_len;   /* longest per-particle candidate list */
+  int32_t status;         /* sticky device status (DEM_OK if none) */
+  int32_t launches_per_step; /* kernels the library launches per time step */
+  int32_t reserved;
+} dem_stats;
+
+typedef struct dem_scene dem_scene;
+
+/* Create a scene on the current CUDA device.  `stream` is a cudaStream_t (NULL:
+ * the library creates its own).  Copies the host arrays to the device.
+ * Errors: DEM_ERR_INVALID (parameters outside Table 2's requirements, n < 1,
+ * non-finite input, bad triangle index), DEM_ERR_NOMEM, DEM_ERR_CUDA. */
+int dem_scene_create(const dem_params* params, const dem_particles* particles,
+                     const dem_mesh* mesh, void* stream, dem_scene** out);
+
+/* Enqueue `nsteps` time steps on the scene's stream and return without
+ * waiting.  Each step: mesh pose, rebuild check, (cell binning, Verlet list and
+ * history remap when needed), contact forces, gather and integration.
+ * Errors found on the device are reported by dem_synchronize(). */
+int dem_step(dem_scene* s, int64_t nsteps);
+
+/* Like dem_step, but launches each step phase by phase (no CUDA graph) with
+ * CUDA events between phases, waits, and adds the elapsed device time of each
+ * phase in milliseconds to phase_ms[0..3]: [0] mesh pose, [1] list rebuild
+ * (binning, permutation, Verlet list, history remap; its kernels return at
+ * once in steps without a rebuild), [2] contact forces + gather + integration,
+ * [3] end-of-step bookkeeping.  For measurement; results are identical to
+ * dem_step.  Errors: as dem_step, plus the sticky device status. */
+int dem_step_timed(dem_scene* s, int64_t nsteps, double* phase_ms);
+
+/* Wait for the scene's stream; return the sticky device status. */
+int dem_synchronize(dem_scene* s);
+
+/* Copy the current state to host arrays in caller order; any pointer may be
+ * NULL.  Synchronizes the stream. */
+int dem_read_state(dem_scene* s, double* x, double* v, double* w, double* q);
+
+/* Contact force and torque sums (no gravity or drag) of the last step, [n][3],
+ * caller order.  Requires params.record_forces.  Synchronizes. */
+int dem_read_forces(dem_scene* s, double* F, double* T);
+
+/* Active contacts of the last step with their friction history.  keys[2k] = i,
+ * keys[2k+1] = j in caller indices: a particle pair has i < j; a triangle
+ * contact has j = -1 - triangle index.  hist[7k..7k+6] = u_s (3), u_r (3), u_t.
+ * Rows are sorted by (i, j).  If `capacity` is too small only the count is
+ * written and DEM_ERR_CAPACITY is returned.  Synchronizes. */
+int dem_read_contacts(dem_scene* s, int64_t capacity, int64_t* keys, double* hist,
+                      int64_t* count);
+
+int dem_get_stats(dem_scene* s, dem_stats* out);
+
+/* Serialise the complete scene (parameters, state, contact history, step
+ * count) into `buf`.  With buf == NULL, writes the required size to *len. */
+int dem_save(dem_scene* s, void* buf, size_t* len);
+
+/* Restore a scene saved by dem_save (same particle count and mesh). */
+int dem_load(dem_scene* s, const void* buf, size_t len);
+
+void dem_scene_destroy(dem_scene* s);
+
+const char* dem_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DEM_H_ */

@@ -1,0 +1,971 @@
+// C ABI of libdem (declared in include/dem.h): scene set-up, memory, the
+// per-step launch sequence (captured once into CUDA graphs), read-back,
+// save/load.  Host code only; kernels live in dem_rebuild.cu, dem_step.cu and
+// dem_scan.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "dem_internal.cuh"
+
+using namespace dem;
+
+namespace {
+
+constexpr int kGraphSteps = 16;  // steps per replay of the long graph
+
+struct Alloc {
+  std::vector<void*> ptrs;
+  bool failed = false;
+  template <typename T>
+  T* get(size_t count) {
+    void* p = nullptr;
+    if (count == 0) count = 1;
+    if (cudaMalloc(&p, count * sizeof(T)) != cudaSuccess) {
+      failed = true;
+      cudaGetLastError();
+      return nullptr;
+    }
+    ptrs.push_back(p);
+    return static_cast<T*>(p);
+  }
+  void release() {
+    for (void* p : ptrs) cudaFree(p);
+    ptrs.clear();
+  }
+};
+
+bool finite_all(const double* a, int64_t n) {
+  for (int64_t i = 0; i < n; ++i)
+    if (!std::isfinite(a[i])) return false;
+  return true;
+}
+
+}  // namespace
+
+struct dem_scene {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  dem_params user{};
+  Params p{};
+  int64_t n = 0;
+  int32_t nv = 0, nt = 0;
+  size_t hist_bytes = 0;  // 64 (FP64) or 32 (mixed)
+  Ctl* ctl = nullptr;
+  StateBufs sb{};
+  Lists L{};
+  BinBuf bb{};
+  MeshDev mesh{};
+  double* forces = nullptr;
+  Alloc mem;
+  cudaGraphExec_t exec1 = nullptr, execG = nullptr;
+  bool static_mesh = true;
+  int32_t launches_per_step = 0;
+};
+
+namespace {
+
+int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return DEM_OK;
+  cudaGetLastError();
+  return e == cudaErrorMemoryAllocation ? DEM_ERR_NOMEM : DEM_ERR_CUDA;
+}
+
+#define DEM_TRY(call)                    \
+  do {                                   \
+    const int rc_ = cuda_status(call);   \
+    if (rc_ != DEM_OK) return rc_;       \
+  } while (0)
+
+int validate(const dem_params* pr, const dem_particles* pa, const dem_mesh* me) {
+  if (!pr || !pa) return DEM_ERR_INVALID;
+  const double sc[] = {pr->E, pr->nu, pr->rho, pr->e_n, pr->mu_s, pr->mu_r, pr->mu_t, pr->eta,
+                       pr->g[0], pr->g[1], pr->g[2], pr->dt, pr->mesh_omega[0],
+                       pr->mesh_omega[1], pr->mesh_omega[2], pr->mesh_center[0],
+                       pr->mesh_center[1], pr->mesh_center[2], pr->skin};
+  if (!finite_all(sc, sizeof sc / sizeof sc[0])) return DEM_ERR_INVALID;
+  // Table 2, "Requirements"
+  if (!(pr->E > 0) || !(pr->nu > -1.0 && pr->nu <= 0.5) || !(pr->rho > 0)) return DEM_ERR_INVALID;
+  if (!(pr->e_n >= 0 && pr->e_n <= 1)) return DEM_ERR_INVALID;
+  if (pr->mu_s < 0 || pr->mu_r < 0 || pr->mu_t < 0 || pr->eta < 0) return DEM_ERR_INVALID;
+  if (!(pr->dt > 0)) return DEM_ERR_INVALID;
+  if (pr->precision != DEM_FP64 && pr->precision != DEM_MIXED) return DEM_ERR_INVALID;
+  if (pr->max_neighbors > 64 || pr->max_mesh_contacts > 255) return DEM_ERR_INVALID;
+  if (pa->n < 1 || pa->n > (int64_t)0x7fffffff / 2) return DEM_ERR_INVALID;
+  if (!pa->R || !pa->x) return DEM_ERR_INVALID;
+  const int64_t n = pa->n;
+  for (int64_t i = 0; i < n; ++i)
+    if (!(pa->R[i] > 0) || !std::isfinite(pa->R[i])) return DEM_ERR_INVALID;
+  if (!finite_all(pa->x, 3 * n)) return DEM_ERR_INVALID;
+  if (pa->v && !finite_all(pa->v, 3 * n)) return DEM_ERR_INVALID;
+  if (pa->w && !finite_all(pa->w, 3 * n)) return DEM_ERR_INVALID;
+  if (pa->q && !finite_all(pa->q, 4 * n)) return DEM_ERR_INVALID;
+  if (me && me->n_tri > 0) {
+    if (!me->vert || !me->tri || me->n_vert < 1 || me->n_tri > 0x7fffffff) return DEM_ERR_INVALID;
+    if (!finite_all(me->vert, 3 * me->n_vert)) return DEM_ERR_INVALID;
+    for (int64_t k = 0; k < 3 * me->n_tri; ++k)
+      if (me->tri[k] < 0 || me->tri[k] >= me->n_vert) return DEM_ERR_INVALID;
+    if (me->tri_radius)
+      for (int64_t k = 0; k < me->n_tri; ++k)
+        if (!(me->tri_radius[k] >= 0) || !std::isfinite(me->tri_radius[k])) return DEM_ERR_INVALID;
+  }
+  return DEM_OK;
+}
+
+double beta_of(double e_n) {
+  if (e_n <= 0.0) return 1.0;
+  if (e_n >= 1.0) return 0.0;
+  const double l = std::log(e_n);
+  const double r = M_PI / l;
+  return 1.0 / std::sqrt(1.0 + r * r);
+}
+
+// Host-side split of a double into the hi/lo pair used by DEM_MIXED.
+inline void split(double a, float& hi, float& lo) {
+  hi = (float)a;
+  lo = (float)(a - (double)hi);
+}
+
+// Enqueue one complete step on the stream.
+void enqueue_step(dem_scene* s) {
+  if (!s->static_mesh) launch_mesh_pose(s->stream, s->ctl, s->p, s->mesh);
+  launch_rebuild(s->stream, s->ctl, s->p, s->sb, s->L, s->bb, s->mesh);
+  launch_step(s->stream, s->ctl, s->p, s->sb, s->L, s->mesh, s->forces);
+  launch_advance(s->stream, s->ctl, s->p);
+}
+
+int build_graph(dem_scene* s, int nsteps, cudaGraphExec_t* out) {
+  cudaGraph_t g = nullptr;
+  DEM_TRY(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
+  for (int i = 0; i < nsteps; ++i) enqueue_step(s);
+  DEM_TRY(cudaStreamEndCapture(s->stream, &g));
+  const cudaError_t e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  return cuda_status(e);
+}
+
+int read_ctl(dem_scene* s, Ctl* c) {
+  DEM_TRY(cudaStreamSynchronize(s->stream));
+  DEM_TRY(cudaMemcpy(c, s->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+  return DEM_OK;
+}
+
+// Host copy of the current state records (slot order) and slot -> caller index.
+struct HostState {
+  std::vector<D4> Pd, Vd, Wd, Qd;
+  std::vector<F8> Pm, Vm, Wm, Qm;
+  std::vector<uint32_t> gid;
+};
+
+int fetch_state(dem_scene* s, const Ctl& c, HostState& h) {
+  const int64_t n = s->n;
+  const uint32_t ph = c.phase & 1u, lph = c.lphase & 1u;
+  h.gid.resize(n);
+  DEM_TRY(cudaMemcpy(h.gid.data(), s->L.b[lph].gid, n * 4, cudaMemcpyDeviceToHost));
+  if (s->p.mixed) {
+    h.Pm.resize(n); h.Vm.resize(n); h.Wm.resize(n); h.Qm.resize(n);
+    DEM_TRY(cudaMemcpy(h.Pm.data(), s->sb.P[ph], n * sizeof(F8), cudaMemcpyDeviceToHost));
+    DEM_TRY(cudaMemcpy(h.Vm.data(), s->sb.V[ph], n * sizeof(F8), cudaMemcpyDeviceToHost));
+    DEM_TRY(cudaMemcpy(h.Wm.data(), s->sb.W[ph], n * sizeof(F8), cudaMemcpyDeviceToHost));
+    DEM_TRY(cudaMemcpy(h.Qm.data(), s->sb.Q[ph], n * sizeof(F8), cudaMemcpyDeviceToHost));
+  } else {
+    h.Pd.resize(n); h.Vd.resize(n); h.Wd.resize(n); h.Qd.resize(n);
+    DEM_TRY(cudaMemcpy(h.Pd.data(), s->sb.P[ph], n * sizeof(D4), cudaMemcpyDeviceToHost));
+    DEM_TRY(cudaMemcpy(h.Vd.data(), s->sb.V[ph], n * sizeof(D4), cudaMemcpyDeviceToHost));
+    DEM_TRY(cudaMemcpy(h.Wd.data(), s->sb.W[ph], n * sizeof(D4), cudaMemcpyDeviceToHost));
+    DEM_TRY(cudaMemcpy(h.Qd.data(), s->sb.Q[ph], n * sizeof(D4), cudaMemcpyDeviceToHost));
+  }
+  return DEM_OK;
+}
+
+struct ContactRow {
+  int64_t i, j;
+  double h[7];
+  uint32_t stamp;
+};
+
+// Active contacts (written in the last step) in caller indices, sorted by (i, j).
+int fetch_contacts(dem_scene* s, const Ctl& c, std::vector<ContactRow>& rows) {
+  const int64_t n = s->n;
+  const uint32_t lph = c.lphase & 1u;
+  const ListBuf& lb = s->L.b[lph];
+  std::vector<uint32_t> gid(n), meta(n);
+  DEM_TRY(cudaMemcpy(gid.data(), lb.gid, n * 4, cudaMemcpyDeviceToHost));
+  DEM_TRY(cudaMemcpy(meta.data(), lb.meta, n * 4, cudaMemcpyDeviceToHost));
+  int maxnn = 0, maxnt = 0;
+  for (int64_t t = 0; t < n; ++t) {
+    maxnn = std::max(maxnn, (int)(meta[t] & 0xffu));
+    maxnt = std::max(maxnt, (int)((meta[t] >> 16) & 0xffu));
+  }
+  std::vector<uint32_t> nbr((size_t)maxnn * n), tric((size_t)maxnt * n);
+  std::vector<unsigned char> hpp((size_t)maxnn * n * s->hist_bytes),
+      hpm((size_t)maxnt * n * s->hist_bytes);
+  if (maxnn) {
+    DEM_TRY(cudaMemcpy(nbr.data(), lb.nbr, nbr.size() * 4, cudaMemcpyDeviceToHost));
+    DEM_TRY(cudaMemcpy(hpp.data(), lb.hpp, hpp.size(), cudaMemcpyDeviceToHost));
+  }
+  if (maxnt) {
+    DEM_TRY(cudaMemcpy(tric.data(), lb.tric, tric.size() * 4, cudaMemcpyDeviceToHost));
+    DEM_TRY(cudaMemcpy(hpm.data(), lb.hpm, hpm.size(), cudaMemcpyDeviceToHost));
+  }
+  const uint32_t want = (uint32_t)c.step;  // stamp written by the last completed step
+  auto decode = [&](const unsigned char* rec, ContactRow& r) {
+    if (s->p.mixed) {
+      HistM h;
+      std::memcpy(&h, rec, sizeof h);
+      for (int q = 0; q < 3; ++q) r.h[q] = h.us[q], r.h[3 + q] = h.ur[q];
+      r.h[6] = h.ut;
+      r.stamp = h.stamp;
+    } else {
+      HistD h;
+      std::memcpy(&h, rec, sizeof h);
+      for (int q = 0; q < 3; ++q) r.h[q] = h.us[q], r.h[3 + q] = h.ur[q];
+      r.h[6] = h.ut;
+      r.stamp = h.stamp;
+    }
+  };
+  rows.clear();
+  for (int64_t t = 0; t < n; ++t) {
+    const int nn = (int)(meta[t] & 0xffu), nt = (int)((meta[t] >> 16) & 0xffu);
+    const int64_t i = gid[t];
+    for (int k = 0; k < nn; ++k) {
+      const uint32_t u = nbr[(size_t)k * n + t];
+      const int64_t j = gid[u];
+      if (j <= i) continue;
+      ContactRow r;
+      decode(&hpp[((size_t)k * n + t) * s->hist_bytes], r);
+      if (r.stamp != want || c.step == 0) continue;
+      r.i = i;
+      r.j = j;
+      rows.push_back(r);
+    }
+    for (int m = 0; m < nt; ++m) {
+      ContactRow r;
+      decode(&hpm[((size_t)m * n + t) * s->hist_bytes], r);
+      if (r.stamp != want || c.step == 0) continue;
+      r.i = i;
+      r.j = -1 - (int64_t)tric[(size_t)m * n + t];
+      rows.push_back(r);
+    }
+  }
+  std::sort(rows.begin(), rows.end(), [](const ContactRow& a, const ContactRow& b) {
+    return a.i != b.i ? a.i < b.i : a.j < b.j;
+  });
+  return DEM_OK;
+}
+
+// Install contacts as the "previous list" of every particle (slot = caller
+// index) so the next rebuild carries their histories over.
+int install_contacts(dem_scene* s, const std::vector<ContactRow>& rows, uint32_t lph,
+                     uint32_t stamp) {
+  const int64_t n = s->n;
+  const ListBuf& lb = s->L.b[lph];
+  std::vector<std::vector<std::pair<int64_t, const ContactRow*>>> pp(n), pm(n);
+  for (const ContactRow& r : rows) {
+    if (r.i < 0 || r.i >= n) return DEM_ERR_INVALID;
+    if (r.j >= 0) {
+      if (r.j >= n || r.j == r.i) return DEM_ERR_INVALID;
+      pp[r.i].push_back({r.j, &r});
+      pp[r.j].push_back({r.i, &r});
+    } else {
+      if (-1 - r.j >= s->nt) return DEM_ERR_INVALID;
+      pm[r.i].push_back({-1 - r.j, &r});
+    }
+  }
+  size_t maxnn = 0, maxnt = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    std::sort(pp[i].begin(), pp[i].end());
+    std::sort(pm[i].begin(), pm[i].end());
+    maxnn = std::max(maxnn, pp[i].size());
+    maxnt = std::max(maxnt, pm[i].size());
+  }
+  if (maxnn > (size_t)s->p.cap || maxnt > (size_t)s->p.capm) return DEM_ERR_CAPACITY;
+  std::vector<uint32_t> meta(n), nbr(maxnn * n), tric(maxnt * n);
+  std::vector<unsigned char> hpp(maxnn * n * s->hist_bytes), hpm(maxnt * n * s->hist_bytes);
+  auto encode = [&](const ContactRow& r, unsigned char* rec) {
+    if (s->p.mixed) {
+      HistM h;
+      for (int q = 0; q < 3; ++q) h.us[q] = (float)r.h[q], h.ur[q] = (float)r.h[3 + q];
+      h.ut = (float)r.h[6];
+      h.stamp = stamp;
+      std::memcpy(rec, &h, sizeof h);
+    } else {
+      HistD h;
+      for (int q = 0; q < 3; ++q) h.us[q] = r.h[q], h.ur[q] = r.h[3 + q];
+      h.ut = r.h[6];
+      h.stamp = stamp;
+      h.pad = 0;
+      std::memcpy(rec, &h, sizeof h);
+    }
+  };
+  for (int64_t i = 0; i < n; ++i) {
+    meta[i] = (uint32_t)pp[i].size() | ((uint32_t)pm[i].size() << 16);
+    for (size_t k = 0; k < pp[i].size(); ++k) {
+      nbr[k * n + i] = (uint32_t)pp[i][k].first;
+      encode(*pp[i][k].second, &hpp[(k * n + i) * s->hist_bytes]);
+    }
+    for (size_t k = 0; k < pm[i].size(); ++k) {
+      tric[k * n + i] = (uint32_t)pm[i][k].first;
+      encode(*pm[i][k].second, &hpm[(k * n + i) * s->hist_bytes]);
+    }
+  }
+  std::vector<uint32_t> ident(n);
+  for (int64_t i = 0; i < n; ++i) ident[i] = (uint32_t)i;
+  DEM_TRY(cudaMemcpy(lb.gid, ident.data(), n * 4, cudaMemcpyHostToDevice));
+  DEM_TRY(cudaMemcpy(lb.meta, meta.data(), n * 4, cudaMemcpyHostToDevice));
+  if (maxnn) {
+    DEM_TRY(cudaMemcpy(lb.nbr, nbr.data(), nbr.size() * 4, cudaMemcpyHostToDevice));
+    DEM_TRY(cudaMemcpy(lb.hpp, hpp.data(), hpp.size(), cudaMemcpyHostToDevice));
+  }
+  if (maxnt) {
+    DEM_TRY(cudaMemcpy(lb.tric, tric.data(), tric.size() * 4, cudaMemcpyHostToDevice));
+    DEM_TRY(cudaMemcpy(lb.hpm, hpm.data(), hpm.size(), cudaMemcpyHostToDevice));
+  }
+  return DEM_OK;
+}
+
+// Upload a state given in caller order (slot = caller index) into buffer 0,
+// reset the control block to (step, lphase 0), and request a rebuild.
+int upload_state(dem_scene* s, const double* x, const double* v, const double* w,
+                 const double* q, const double* R, int64_t step) {
+  const int64_t n = s->n;
+  const double rho = s->p.rho;
+  if (s->p.mixed) {
+    std::vector<F8> P(n), V(n), W(n), Q(n);
+    for (int64_t i = 0; i < n; ++i) {
+      const double m = 4.0 / 3.0 * M_PI * rho * R[i] * R[i] * R[i];
+      split(x[3 * i] - s->p.origin[0], P[i].hi.x, P[i].lo.x);
+      split(x[3 * i + 1] - s->p.origin[1], P[i].hi.y, P[i].lo.y);
+      split(x[3 * i + 2] - s->p.origin[2], P[i].hi.z, P[i].lo.z);
+      split(R[i], P[i].hi.w, P[i].lo.w);
+      split(v ? v[3 * i] : 0.0, V[i].hi.x, V[i].lo.x);
+      split(v ? v[3 * i + 1] : 0.0, V[i].hi.y, V[i].lo.y);
+      split(v ? v[3 * i + 2] : 0.0, V[i].hi.z, V[i].lo.z);
+      V[i].hi.w = (float)m;
+      V[i].lo.w = 0.f;
+      split(w ? w[3 * i] : 0.0, W[i].hi.x, W[i].lo.x);
+      split(w ? w[3 * i + 1] : 0.0, W[i].hi.y, W[i].lo.y);
+      split(w ? w[3 * i + 2] : 0.0, W[i].hi.z, W[i].lo.z);
+      W[i].hi.w = W[i].lo.w = 0.f;
+      split(q ? q[4 * i] : 1.0, Q[i].hi.x, Q[i].lo.x);
+      split(q ? q[4 * i + 1] : 0.0, Q[i].hi.y, Q[i].lo.y);
+      split(q ? q[4 * i + 2] : 0.0, Q[i].hi.z, Q[i].lo.z);
+      split(q ? q[4 * i + 3] : 0.0, Q[i].hi.w, Q[i].lo.w);
+    }
+    DEM_TRY(cudaMemcpy(s->sb.P[0], P.data(), n * sizeof(F8), cudaMemcpyHostToDevice));
+    DEM_TRY(cudaMemcpy(s->sb.V[0], V.data(), n * sizeof(F8), cudaMemcpyHostToDevice));
+    DEM_TRY(cudaMemcpy(s->sb.W[0], W.data(), n * sizeof(F8), cudaMemcpyHostToDevice));
+    DEM_TRY(cudaMemcpy(s->sb.Q[0], Q.data(), n * sizeof(F8), cudaMemcpyHostToDevice));
+  } else {
+    std::vector<D4> P(n), V(n), W(n), Q(n);
+    for (int64_t i = 0; i < n; ++i) {
+      const double m = 4.0 / 3.0 * M_PI * rho * R[i] * R[i] * R[i];
+      P[i] = make_D4(x[3 * i], x[3 * i + 1], x[3 * i + 2], R[i]);
+      V[i] = v ? make_D4(v[3 * i], v[3 * i + 1], v[3 * i + 2], m) : make_D4(0, 0, 0, m);
+      W[i] = w ? make_D4(w[3 * i], w[3 * i + 1], w[3 * i + 2], 0) : make_D4(0, 0, 0, 0);
+      Q[i] = q ? make_D4(q[4 * i], q[4 * i + 1], q[4 * i + 2], q[4 * i + 3])
+               : make_D4(1, 0, 0, 0);
+    }
+    DEM_TRY(cudaMemcpy(s->sb.P[0], P.data(), n * sizeof(D4), cudaMemcpyHostToDevice));
+    DEM_TRY(cudaMemcpy(s->sb.V[0], V.data(), n * sizeof(D4), cudaMemcpyHostToDevice));
+    DEM_TRY(cudaMemcpy(s->sb.W[0], W.data(), n * sizeof(D4), cudaMemcpyHostToDevice));
+    DEM_TRY(cudaMemcpy(s->sb.Q[0], Q.data(), n * sizeof(D4), cudaMemcpyHostToDevice));
+  }
+  std::vector<uint32_t> ident(n);
+  for (int64_t i = 0; i < n; ++i) ident[i] = (uint32_t)i;
+  for (int b = 0; b < 2; ++b) {
+    DEM_TRY(cudaMemcpy(s->L.b[b].gid, ident.data(), n * 4, cudaMemcpyHostToDevice));
+    DEM_TRY(cudaMemset(s->L.b[b].meta, 0, n * 4));
+  }
+  Ctl c{};
+  c.step = step;
+  c.rebuild = 1;
+  DEM_TRY(cudaMemcpy(s->ctl, &c, sizeof c, cudaMemcpyHostToDevice));
+  return DEM_OK;
+}
+
+void destroy(dem_scene* s) {
+  if (!s) return;
+  if (s->exec1) cudaGraphExecDestroy(s->exec1);
+  if (s->execG) cudaGraphExecDestroy(s->execG);
+  if (s->stream) cudaStreamSynchronize(s->stream);
+  s->mem.release();
+  if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+  delete s;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* dem_status_string(int status) {
+  switch (status) {
+    case DEM_OK: return "ok";
+    case DEM_ERR_INVALID: return "invalid argument";
+    case DEM_ERR_CAPACITY: return "list capacity exceeded";
+    case DEM_ERR_NONFINITE: return "non-finite particle state";
+    case DEM_ERR_TIMEOUT: return "device wait timed out";
+    case DEM_ERR_CUDA: return "CUDA error";
+    case DEM_ERR_NOMEM: return "out of device memory";
+    default: return "unknown status";
+  }
+}
+
+int dem_scene_create(const dem_params* params, const dem_particles* parts, const dem_mesh* mesh,
+                     void* stream, dem_scene** out) {
+  if (!out) return DEM_ERR_INVALID;
+  *out = nullptr;
+  int rc = validate(params, parts, mesh);
+  if (rc != DEM_OK) return rc;
+  dem_scene* s = new (std::nothrow) dem_scene();
+  if (!s) return DEM_ERR_NOMEM;
+  auto fail = [&](int code) {
+    destroy(s);
+    return code;
+  };
+  if (cudaGetDevice(&s->device) != cudaSuccess) return fail(DEM_ERR_CUDA);
+  if (stream) {
+    s->stream = static_cast<cudaStream_t>(stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess)
+      return fail(DEM_ERR_CUDA);
+    s->own_stream = true;
+  }
+  s->user = *params;
+  const int64_t n = parts->n;
+  s->n = n;
+  const bool has_mesh = mesh && mesh->n_tri > 0;
+  s->nt = has_mesh ? (int32_t)mesh->n_tri : 0;
+  s->nv = has_mesh ? (int32_t)mesh->n_vert : 0;
+  Params& p = s->p;
+  p.E = params->E;
+  p.nu = params->nu;
+  p.rho = params->rho;
+  p.e_n = params->e_n;
+  p.mu_s = params->mu_s;
+  p.mu_r = params->mu_r;
+  p.mu_t = params->mu_t;
+  p.eta = params->eta;
+  p.dt = params->dt;
+  for (int a = 0; a < 3; ++a) {
+    p.g[a] = params->g[a];
+    p.mesh_omega[a] = params->mesh_omega[a];
+    p.mesh_center[a] = params->mesh_center[a];
+  }
+  p.beta = beta_of(p.e_n);
+  {
+    const double E = p.E, nu = p.nu, G = E / (2.0 * (1.0 + nu));
+    p.Es_pp = 1.0 / ((1.0 - nu * nu) / E + (1.0 - nu * nu) / E);
+    p.Gs_pp = 1.0 / ((2.0 - nu) / G + (2.0 - nu) / G);
+    p.Es_pw = 1.0 / ((1.0 - nu * nu) / E);
+    p.Gs_pw = 1.0 / ((2.0 - nu) / G);
+  }
+  p.omega_norm = std::sqrt(p.mesh_omega[0] * p.mesh_omega[0] + p.mesh_omega[1] * p.mesh_omega[1] +
+                           p.mesh_omega[2] * p.mesh_omega[2]);
+  s->static_mesh = !(p.omega_norm > 0.0);
+  p.mixed = params->precision == DEM_MIXED ? 1 : 0;
+  p.record_forces = params->record_forces ? 1 : 0;
+  p.n = (int32_t)n;
+  p.n_tri = s->nt;
+  p.cap = params->max_neighbors > 0 ? params->max_neighbors : 64;
+  p.capm = params->max_mesh_contacts > 0 ? params->max_mesh_contacts : 16;
+  s->hist_bytes = p.mixed ? sizeof(HistM) : sizeof(HistD);
+
+  // radii, skin, domain
+  double rmax = 0, rmin = INFINITY;
+  for (int64_t i = 0; i < n; ++i) {
+    rmax = std::max(rmax, parts->R[i]);
+    rmin = std::min(rmin, parts->R[i]);
+  }
+  const double skin = params->skin > 0 ? params->skin : 0.25 * rmax;
+  double lo[3], hi[3];
+  bool user_box = true;
+  for (int a = 0; a < 3; ++a)
+    if (!(params->domain_lo[a] < params->domain_hi[a])) user_box = false;
+  if (user_box) {
+    for (int a = 0; a < 3; ++a) lo[a] = params->domain_lo[a], hi[a] = params->domain_hi[a];
+  } else {
+    for (int a = 0; a < 3; ++a) lo[a] = INFINITY, hi[a] = -INFINITY;
+    for (int64_t i = 0; i < n; ++i)
+      for (int a = 0; a < 3; ++a) {
+        lo[a] = std::min(lo[a], parts->x[3 * i + a]);
+        hi[a] = std::max(hi[a], parts->x[3 * i + a]);
+      }
+    double mrad = 0;
+    if (has_mesh) {
+      double rtri = 0;
+      if (mesh->tri_radius)
+        for (int64_t k = 0; k < mesh->n_tri; ++k) rtri = std::max(rtri, mesh->tri_radius[k]);
+      for (int64_t k = 0; k < mesh->n_vert; ++k)
+        for (int a = 0; a < 3; ++a) {
+          lo[a] = std::min(lo[a], mesh->vert[3 * k + a] - rtri);
+          hi[a] = std::max(hi[a], mesh->vert[3 * k + a] + rtri);
+        }
+      mrad = rtri;
+    }
+    if (has_mesh && !s->static_mesh) {
+      // a turning mesh: each vertex sweeps a circle about the axis; on axis a
+      // that circle spans c_a + s ax_a +- r sqrt(1 - ax_a^2) (s: coordinate
+      // along the axis, r: distance from it)
+      double ax[3];
+      for (int a = 0; a < 3; ++a) ax[a] = p.mesh_omega[a] / p.omega_norm;
+      for (int64_t k = 0; k < mesh->n_vert; ++k) {
+        double d[3], along = 0, r2 = 0;
+        for (int a = 0; a < 3; ++a) {
+          d[a] = mesh->vert[3 * k + a] - p.mesh_center[a];
+          along += d[a] * ax[a];
+        }
+        for (int a = 0; a < 3; ++a) {
+          const double perp = d[a] - along * ax[a];
+          r2 += perp * perp;
+        }
+        const double r = std::sqrt(r2);
+        for (int a = 0; a < 3; ++a) {
+          const double half = r * std::sqrt(std::max(0.0, 1.0 - ax[a] * ax[a]));
+          const double c = p.mesh_center[a] + along * ax[a];
+          lo[a] = std::min(lo[a], c - half - mrad);
+          hi[a] = std::max(hi[a], c + half + mrad);
+        }
+      }
+    }
+    const double pad = 2.0 * rmax + skin;
+    for (int a = 0; a < 3; ++a) lo[a] -= pad, hi[a] += pad;
+  }
+  // Shifted coordinates X = x - origin, with X in [B, 2B) on each axis (B a
+  // power of two), so the hi words of two positions share a binade and their
+  // difference is exact.  The frame depends only on the binning box without
+  // the skin, so DEM_MIXED rounding does not change with the skin.
+  double bmax = 0;
+  for (int a = 0; a < 3; ++a) {
+    const double flo = lo[a] + (user_box ? 0.0 : skin);
+    const double fhi = hi[a] - (user_box ? 0.0 : skin);
+    const double ext = std::max(fhi - flo, 1e-300);
+    const double B = std::ldexp(1.0, (int)std::ceil(std::log2(ext)));
+    p.origin[a] = flo - B;
+    p.base[a] = lo[a] - p.origin[a];  // grid corner in shifted coordinates
+    bmax = std::max(bmax, B);
+  }
+  const double ulp_top = std::ldexp(2.0 * bmax, -23);
+  const double cut0 = 2.0 * rmax + skin;
+  p.list_margin = (float)(4.0 * ulp_top + 1e-6 * cut0);
+  const double h = cut0 * (1.0 + 1e-6) + 2.0 * p.list_margin;
+  p.h = (float)h;
+  p.inv_h = (float)(1.0 / h);
+  int64_t ncells = 1;
+  for (int a = 0; a < 3; ++a) {
+    const int64_t c = std::max<int64_t>(1, (int64_t)std::ceil((hi[a] - lo[a]) / h));
+    if (c > (1 << 20)) return fail(DEM_ERR_INVALID);
+    p.nc[a] = (int32_t)c;
+    ncells *= c;
+  }
+  if (ncells > ((int64_t)1 << 30)) return fail(DEM_ERR_INVALID);
+  p.ncells = ncells;
+  p.skin = (float)skin;
+  p.half_skin_trigger = (float)(0.5 * skin - 4.0 * ulp_top);
+  if (!(p.half_skin_trigger > 0)) return fail(DEM_ERR_INVALID);
+  p.rmax = (float)rmax;
+  p.mesh_prefilter = (float)(16.0 * ulp_top);
+  for (int a = 0; a < 3; ++a) split(p.mesh_center[a] - p.origin[a], p.center_hi[a], p.center_lo[a]);
+  p.mesh_rmax = 0;
+  if (has_mesh && !s->static_mesh) {
+    const double ax[3] = {p.mesh_omega[0] / p.omega_norm, p.mesh_omega[1] / p.omega_norm,
+                          p.mesh_omega[2] / p.omega_norm};
+    for (int64_t k = 0; k < mesh->n_vert; ++k) {
+      double d[3], dd = 0, along = 0;
+      for (int a = 0; a < 3; ++a) {
+        d[a] = mesh->vert[3 * k + a] - p.mesh_center[a];
+        along += d[a] * ax[a];
+      }
+      for (int a = 0; a < 3; ++a) {
+        const double perp = d[a] - along * ax[a];
+        dd += perp * perp;
+      }
+      p.mesh_rmax = std::max(p.mesh_rmax, std::sqrt(dd));
+    }
+  }
+
+  // device memory
+  Alloc& M = s->mem;
+  s->ctl = M.get<Ctl>(1);
+  const size_t rec = p.mixed ? sizeof(F8) : sizeof(D4);
+  for (int b = 0; b < 2; ++b) {
+    s->sb.P[b] = M.get<unsigned char>(n * rec);
+    s->sb.V[b] = M.get<unsigned char>(n * rec);
+    s->sb.W[b] = M.get<unsigned char>(n * rec);
+    s->sb.Q[b] = M.get<unsigned char>(n * rec);
+    ListBuf& lb = s->L.b[b];
+    lb.gid = M.get<uint32_t>(n);
+    lb.posf = M.get<float4>(n);
+    lb.meta = M.get<uint32_t>(n);
+    lb.nbr = M.get<uint32_t>((size_t)p.cap * n);
+    lb.hpp = M.get<unsigned char>((size_t)p.cap * n * s->hist_bytes);
+    if (has_mesh) {
+      lb.tric = M.get<uint32_t>((size_t)p.capm * n);
+      lb.hpm = M.get<unsigned char>((size_t)p.capm * n * s->hist_bytes);
+    }
+  }
+  s->bb.key = M.get<uint32_t>(n);
+  s->bb.local = M.get<uint32_t>(n);
+  s->bb.order = M.get<uint32_t>(n);
+  s->bb.cell_count = M.get<uint32_t>(ncells);
+  s->bb.cell_start = M.get<uint32_t>(ncells + 1);
+  s->bb.block_sums = M.get<uint32_t>(scan_block_sums_size(ncells) + 1);
+  if (p.record_forces) s->forces = M.get<double>(6 * (size_t)n);
+  if (has_mesh) {
+    s->bb.tcell_count = M.get<uint32_t>(ncells);
+    s->bb.tcell_start = M.get<uint32_t>(ncells + 1);
+    s->bb.tcell_overflow = M.get<uint32_t>(1);
+    // capacity: for every triangle, the cells of a cube around its bounding
+    // ball grown by the reach (valid for any pose of a rigid mesh)
+    const double reach = rmax + skin + 2.0 * p.list_margin;
+    double tcap = 0;
+    for (int64_t k = 0; k < mesh->n_tri; ++k) {
+      double c[3] = {0, 0, 0};
+      for (int j = 0; j < 3; ++j)
+        for (int a = 0; a < 3; ++a) c[a] += mesh->vert[3 * mesh->tri[3 * k + j] + a] / 3.0;
+      double rb = 0;
+      for (int j = 0; j < 3; ++j) {
+        double d2 = 0;
+        for (int a = 0; a < 3; ++a) {
+          const double d = mesh->vert[3 * mesh->tri[3 * k + j] + a] - c[a];
+          d2 += d * d;
+        }
+        rb = std::max(rb, std::sqrt(d2));
+      }
+      const double rk = mesh->tri_radius ? mesh->tri_radius[k] : 0.0;
+      const double side = std::ceil(2.0 * (rb + rk + reach) / h) + 2.0;
+      tcap += std::min((double)ncells, side * side * side);
+    }
+    if (tcap > 2.0e9) return fail(DEM_ERR_NOMEM);
+    s->bb.tcap = (uint32_t)tcap + 1024;
+    s->bb.tcell_tri = M.get<uint32_t>(s->bb.tcap);
+    s->mesh.ref = M.get<D4>(s->nv);
+    s->mesh.tri = M.get<int4>(s->nt);
+    s->mesh.rad = M.get<double>(s->nt);
+    s->mesh.cur = M.get<D4>(3 * (size_t)s->nt);
+    s->mesh.curf = M.get<float4>(3 * (size_t)s->nt);
+  }
+  if (M.failed) return fail(DEM_ERR_NOMEM);
+  s->mesh.nv = s->nv;
+  s->mesh.nt = s->nt;
+
+  if (has_mesh) {
+    std::vector<D4> ref(s->nv);
+    for (int k = 0; k < s->nv; ++k)
+      ref[k] = make_D4(mesh->vert[3 * k], mesh->vert[3 * k + 1], mesh->vert[3 * k + 2], 0);
+    std::vector<int4> tri(s->nt);
+    std::vector<double> rad(s->nt);
+    for (int k = 0; k < s->nt; ++k) {
+      tri[k] = make_int4(mesh->tri[3 * k], mesh->tri[3 * k + 1], mesh->tri[3 * k + 2], 0);
+      rad[k] = mesh->tri_radius ? mesh->tri_radius[k] : 0.0;
+    }
+    if (cudaMemcpy(s->mesh.ref, ref.data(), s->nv * sizeof(D4), cudaMemcpyHostToDevice) ||
+        cudaMemcpy(s->mesh.tri, tri.data(), s->nt * sizeof(int4), cudaMemcpyHostToDevice) ||
+        cudaMemcpy(s->mesh.rad, rad.data(), s->nt * sizeof(double), cudaMemcpyHostToDevice))
+      return fail(DEM_ERR_CUDA);
+  }
+  // kernels per step: mesh pose, rebuild (prep, clear, count, 3 scan, scatter,
+  // cell sort, permute, [mesh: clear, count, 3 scan, check, clear, fill, sort],
+  // list build, end), step, advance
+  s->launches_per_step = (s->static_mesh ? 0 : 1) + 11 + (has_mesh ? 9 : 0) + 2;
+  rc = upload_state(s, parts->x, parts->v, parts->w, parts->q, parts->R, 0);
+  if (rc != DEM_OK) return fail(rc);
+  // pose at step 0 (a static mesh keeps it)
+  launch_mesh_pose(s->stream, s->ctl, s->p, s->mesh);
+  if (cudaStreamSynchronize(s->stream) != cudaSuccess) return fail(DEM_ERR_CUDA);
+  *out = s;
+  return DEM_OK;
+}
+
+int dem_step(dem_scene* s, int64_t nsteps) {
+  if (!s || nsteps < 0) return DEM_ERR_INVALID;
+  if (nsteps == 0) return DEM_OK;
+  if (!s->exec1) {
+    int rc = build_graph(s, 1, &s->exec1);
+    if (rc != DEM_OK) return rc;
+    rc = build_graph(s, kGraphSteps, &s->execG);
+    if (rc != DEM_OK) return rc;
+  }
+  int64_t left = nsteps;
+  while (left >= kGraphSteps) {
+    DEM_TRY(cudaGraphLaunch(s->execG, s->stream));
+    left -= kGraphSteps;
+  }
+  while (left-- > 0) DEM_TRY(cudaGraphLaunch(s->exec1, s->stream));
+  return DEM_OK;
+}
+
+int dem_step_timed(dem_scene* s, int64_t nsteps, double* phase_ms) {
+  if (!s || nsteps < 0 || !phase_ms) return DEM_ERR_INVALID;
+  cudaEvent_t ev[5];
+  for (int i = 0; i < 5; ++i)
+    if (cudaEventCreate(&ev[i]) != cudaSuccess) {
+      for (int j = 0; j < i; ++j) cudaEventDestroy(ev[j]);
+      return DEM_ERR_CUDA;
+    }
+  int rc = DEM_OK;
+  double acc[4] = {0, 0, 0, 0};
+  for (int64_t k = 0; k < nsteps && rc == DEM_OK; ++k) {
+    cudaEventRecord(ev[0], s->stream);
+    if (!s->static_mesh) launch_mesh_pose(s->stream, s->ctl, s->p, s->mesh);
+    cudaEventRecord(ev[1], s->stream);
+    launch_rebuild(s->stream, s->ctl, s->p, s->sb, s->L, s->bb, s->mesh);
+    cudaEventRecord(ev[2], s->stream);
+    launch_step(s->stream, s->ctl, s->p, s->sb, s->L, s->mesh, s->forces);
+    cudaEventRecord(ev[3], s->stream);
+    launch_advance(s->stream, s->ctl, s->p);
+    cudaEventRecord(ev[4], s->stream);
+    rc = cuda_status(cudaEventSynchronize(ev[4]));
+    for (int i = 0; i < 4 && rc == DEM_OK; ++i) {
+      float ms = 0.f;
+      rc = cuda_status(cudaEventElapsedTime(&ms, ev[i], ev[i + 1]));
+      acc[i] += ms;
+    }
+  }
+  for (int i = 0; i < 5; ++i) cudaEventDestroy(ev[i]);
+  for (int i = 0; i < 4; ++i) phase_ms[i] += acc[i];
+  if (rc != DEM_OK) return rc;
+  return dem_synchronize(s);
+}
+
+int dem_synchronize(dem_scene* s) {
+  if (!s) return DEM_ERR_INVALID;
+  Ctl c;
+  int rc = read_ctl(s, &c);
+  if (rc != DEM_OK) return rc;
+  return (int)c.status;
+}
+
+int dem_read_state(dem_scene* s, double* x, double* v, double* w, double* q) {
+  if (!s) return DEM_ERR_INVALID;
+  Ctl c;
+  int rc = read_ctl(s, &c);
+  if (rc != DEM_OK) return rc;
+  HostState h;
+  rc = fetch_state(s, c, h);
+  if (rc != DEM_OK) return rc;
+  const int64_t n = s->n;
+  for (int64_t t = 0; t < n; ++t) {
+    const int64_t i = h.gid[t];
+    if (s->p.mixed) {
+      const F8 &P = h.Pm[t], &V = h.Vm[t], &W = h.Wm[t], &Q = h.Qm[t];
+      if (x) {
+        x[3 * i] = s->p.origin[0] + ((double)P.hi.x + (double)P.lo.x);
+        x[3 * i + 1] = s->p.origin[1] + ((double)P.hi.y + (double)P.lo.y);
+        x[3 * i + 2] = s->p.origin[2] + ((double)P.hi.z + (double)P.lo.z);
+      }
+      if (v) {
+        v[3 * i] = (double)V.hi.x + (double)V.lo.x;
+        v[3 * i + 1] = (double)V.hi.y + (double)V.lo.y;
+        v[3 * i + 2] = (double)V.hi.z + (double)V.lo.z;
+      }
+      if (w) {
+        w[3 * i] = (double)W.hi.x + (double)W.lo.x;
+        w[3 * i + 1] = (double)W.hi.y + (double)W.lo.y;
+        w[3 * i + 2] = (double)W.hi.z + (double)W.lo.z;
+      }
+      if (q) {
+        q[4 * i] = (double)Q.hi.x + (double)Q.lo.x;
+        q[4 * i + 1] = (double)Q.hi.y + (double)Q.lo.y;
+        q[4 * i + 2] = (double)Q.hi.z + (double)Q.lo.z;
+        q[4 * i + 3] = (double)Q.hi.w + (double)Q.lo.w;
+      }
+    } else {
+      const D4 &P = h.Pd[t], &V = h.Vd[t], &W = h.Wd[t], &Q = h.Qd[t];
+      if (x) x[3 * i] = P.x, x[3 * i + 1] = P.y, x[3 * i + 2] = P.z;
+      if (v) v[3 * i] = V.x, v[3 * i + 1] = V.y, v[3 * i + 2] = V.z;
+      if (w) w[3 * i] = W.x, w[3 * i + 1] = W.y, w[3 * i + 2] = W.z;
+      if (q) q[4 * i] = Q.x, q[4 * i + 1] = Q.y, q[4 * i + 2] = Q.z, q[4 * i + 3] = Q.w;
+    }
+  }
+  return (int)c.status;
+}
+
+int dem_read_forces(dem_scene* s, double* F, double* T) {
+  if (!s || !s->forces) return DEM_ERR_INVALID;
+  Ctl c;
+  int rc = read_ctl(s, &c);
+  if (rc != DEM_OK) return rc;
+  const int64_t n = s->n;
+  std::vector<double> f(6 * (size_t)n);
+  std::vector<uint32_t> gid(n);
+  DEM_TRY(cudaMemcpy(f.data(), s->forces, f.size() * 8, cudaMemcpyDeviceToHost));
+  DEM_TRY(cudaMemcpy(gid.data(), s->L.b[c.lphase & 1u].gid, n * 4, cudaMemcpyDeviceToHost));
+  for (int64_t t = 0; t < n; ++t) {
+    const int64_t i = gid[t];
+    for (int a = 0; a < 3; ++a) {
+      if (F) F[3 * i + a] = f[6 * t + a];
+      if (T) T[3 * i + a] = f[6 * t + 3 + a];
+    }
+  }
+  return (int)c.status;
+}
+
+int dem_read_contacts(dem_scene* s, int64_t capacity, int64_t* keys, double* hist,
+                      int64_t* count) {
+  if (!s || !count) return DEM_ERR_INVALID;
+  Ctl c;
+  int rc = read_ctl(s, &c);
+  if (rc != DEM_OK) return rc;
+  std::vector<ContactRow> rows;
+  rc = fetch_contacts(s, c, rows);
+  if (rc != DEM_OK) return rc;
+  *count = (int64_t)rows.size();
+  if ((int64_t)rows.size() > capacity) return DEM_ERR_CAPACITY;
+  for (size_t k = 0; k < rows.size(); ++k) {
+    if (keys) keys[2 * k] = rows[k].i, keys[2 * k + 1] = rows[k].j;
+    if (hist) std::memcpy(hist + 7 * k, rows[k].h, 7 * sizeof(double));
+  }
+  return (int)c.status;
+}
+
+int dem_get_stats(dem_scene* s, dem_stats* out) {
+  if (!s || !out) return DEM_ERR_INVALID;
+  Ctl c;
+  int rc = read_ctl(s, &c);
+  if (rc != DEM_OK) return rc;
+  out->steps = c.step;
+  out->rebuilds = c.rebuilds;
+  out->pair_contacts = c.pair_contacts_last / 2;
+  out->mesh_contacts = c.mesh_contacts_last;
+  out->list_entries = c.list_entries;
+  out->mesh_candidates = c.mesh_candidates;
+  out->max_list_len = (int32_t)c.max_list_len;
+  out->status = (int32_t)c.status;
+  out->launches_per_step = s->launches_per_step;
+  out->reserved = 0;
+  return DEM_OK;
+}
+
+// Save format (little-endian, native struct layout):
+//   u64 magic, u64 version, i64 n, i64 n_tri, dem_params, i64 step,
+//   n records P, V, W, Q in caller order (D4 or F8 by precision),
+//   n radii (double), i64 m, m x (i64 i, i64 j, double h[7]).
+static const uint64_t kMagic = 0x4d45445f42503347ull;  // "G3PB_DEM"
+
+int dem_save(dem_scene* s, void* buf, size_t* len) {
+  if (!s || !len) return DEM_ERR_INVALID;
+  Ctl c;
+  int rc = read_ctl(s, &c);
+  if (rc != DEM_OK) return rc;
+  if (c.status) return (int)c.status;
+  HostState h;
+  rc = fetch_state(s, c, h);
+  if (rc != DEM_OK) return rc;
+  std::vector<ContactRow> rows;
+  rc = fetch_contacts(s, c, rows);
+  if (rc != DEM_OK) return rc;
+  const int64_t n = s->n;
+  const size_t rec = s->p.mixed ? sizeof(F8) : sizeof(D4);
+  const size_t need = 8 * 4 + sizeof(dem_params) + 8 + 4 * n * rec + 8 * n + 8 +
+                      rows.size() * (16 + 56);
+  if (!buf) {
+    *len = need;
+    return DEM_OK;
+  }
+  if (*len < need) {
+    *len = need;
+    return DEM_ERR_CAPACITY;
+  }
+  unsigned char* o = static_cast<unsigned char*>(buf);
+  auto put = [&](const void* src, size_t b) {
+    std::memcpy(o, src, b);
+    o += b;
+  };
+  const uint64_t ver = 1;
+  const int64_t nt = s->nt;
+  put(&kMagic, 8);
+  put(&ver, 8);
+  put(&n, 8);
+  put(&nt, 8);
+  put(&s->user, sizeof(dem_params));
+  put(&c.step, 8);
+  // records in caller order
+  std::vector<unsigned char> tmp(n * rec);
+  for (int part = 0; part < 4; ++part) {
+    for (int64_t t = 0; t < n; ++t) {
+      const int64_t i = h.gid[t];
+      const void* src;
+      if (s->p.mixed)
+        src = part == 0 ? (const void*)&h.Pm[t] : part == 1 ? (const void*)&h.Vm[t]
+              : part == 2 ? (const void*)&h.Wm[t] : (const void*)&h.Qm[t];
+      else
+        src = part == 0 ? (const void*)&h.Pd[t] : part == 1 ? (const void*)&h.Vd[t]
+              : part == 2 ? (const void*)&h.Wd[t] : (const void*)&h.Qd[t];
+      std::memcpy(&tmp[i * rec], src, rec);
+    }
+    put(tmp.data(), n * rec);
+  }
+  std::vector<double> R(n);
+  for (int64_t t = 0; t < n; ++t) {
+    const int64_t i = h.gid[t];
+    R[i] = s->p.mixed ? (double)h.Pm[t].hi.w + (double)h.Pm[t].lo.w : h.Pd[t].w;
+  }
+  put(R.data(), 8 * n);
+  const int64_t m = (int64_t)rows.size();
+  put(&m, 8);
+  for (const ContactRow& r : rows) {
+    put(&r.i, 8);
+    put(&r.j, 8);
+    put(r.h, 56);
+  }
+  *len = need;
+  return DEM_OK;
+}
+
+int dem_load(dem_scene* s, const void* buf, size_t len) {
+  if (!s || !buf) return DEM_ERR_INVALID;
+  const unsigned char* in = static_cast<const unsigned char*>(buf);
+  const unsigned char* end = in + len;
+  auto get = [&](void* dst, size_t b) {
+    if (in + b > end) return false;
+    std::memcpy(dst, in, b);
+    in += b;
+    return true;
+  };
+  uint64_t magic, ver;
+  int64_t n, nt, step;
+  dem_params up;
+  if (!get(&magic, 8) || !get(&ver, 8) || !get(&n, 8) || !get(&nt, 8)) return DEM_ERR_INVALID;
+  if (magic != kMagic || ver != 1 || n != s->n || nt != s->nt) return DEM_ERR_INVALID;
+  if (!get(&up, sizeof up) || !get(&step, 8)) return DEM_ERR_INVALID;
+  if (up.precision != s->user.precision) return DEM_ERR_INVALID;
+  const size_t rec = s->p.mixed ? sizeof(F8) : sizeof(D4);
+  if (in + 4 * n * rec + 8 * n + 8 > end) return DEM_ERR_INVALID;
+  DEM_TRY(cudaStreamSynchronize(s->stream));
+  void* dst[4] = {s->sb.P[0], s->sb.V[0], s->sb.W[0], s->sb.Q[0]};
+  for (int part = 0; part < 4; ++part) {
+    DEM_TRY(cudaMemcpy(dst[part], in, n * rec, cudaMemcpyHostToDevice));
+    in += n * rec;
+  }
+  in += 8 * n;  // radii (already inside the P records)
+  int64_t m;
+  if (!get(&m, 8) || m < 0) return DEM_ERR_INVALID;
+  std::vector<ContactRow> rows(m);
+  for (int64_t k = 0; k < m; ++k) {
+    if (!get(&rows[k].i, 8) || !get(&rows[k].j, 8) || !get(rows[k].h, 56)) return DEM_ERR_INVALID;
+  }
+  std::vector<uint32_t> ident(n);
+  for (int64_t i = 0; i < n; ++i) ident[i] = (uint32_t)i;
+  for (int b = 0; b < 2; ++b) {
+    DEM_TRY(cudaMemcpy(s->L.b[b].gid, ident.data(), n * 4, cudaMemcpyHostToDevice));
+    DEM_TRY(cudaMemset(s->L.b[b].meta, 0, n * 4));
+  }
+  int rc = install_contacts(s, rows, 0, (uint32_t)step);
+  if (rc != DEM_OK) return rc;
+  Ctl c{};
+  c.step = step;
+  c.rebuild = 1;
+  DEM_TRY(cudaMemcpy(s->ctl, &c, sizeof c, cudaMemcpyHostToDevice));
+  launch_mesh_pose(s->stream, s->ctl, s->p, s->mesh);
+  DEM_TRY(cudaStreamSynchronize(s->stream));
+  return DEM_OK;
+}
+
+void dem_scene_destroy(dem_scene* s) { destroy(s); }
+
+}  // extern "C"

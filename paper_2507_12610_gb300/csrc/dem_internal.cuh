@@ -1,0 +1,177 @@
+// Internal types shared by the libdem translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dem.h"
+
+namespace dem {
+
+// 32-byte aligned record of four doubles (one DRAM sector per load).
+using D4 = double4_32a;
+__host__ __device__ __forceinline__ D4 make_D4(double x, double y, double z, double w) {
+  return make_double4_32a(x, y, z, w);
+}
+
+// ---------------------------------------------------------------------------
+// Device control block: one per scene, in device memory.  All per-step
+// decisions (rebuild or not, which buffer is current) live here so a step is
+// a fixed kernel sequence that can be captured in a CUDA graph.
+struct Ctl {
+  uint32_t status;      // sticky error code (DEM_OK = 0)
+  uint32_t phase;       // index of the current dynamic-state buffer (0/1)
+  uint32_t lphase;      // index of the current list/history buffer (0/1)
+  uint32_t rebuild;     // 1 while the current step rebuilds the lists
+  uint32_t disp_flag;   // set by the step kernel: some particle moved > skin/2
+  uint32_t force_rebuild;
+  int64_t step;         // steps completed
+  int64_t rebuilds;
+  double mesh_angle_ref;  // mesh rotation angle at the last rebuild
+  uint32_t pair_contacts;  // touching directed pair entries, this step (accumulating)
+  uint32_t mesh_contacts;
+  uint32_t pair_contacts_last;  // ... of the last completed step
+  uint32_t mesh_contacts_last;
+  uint32_t list_entries;     // directed candidate entries of the current list
+  uint32_t mesh_candidates;
+  uint32_t max_list_len;
+  uint32_t pad0;
+};
+
+// Parameters the kernels need, passed by value.
+struct Params {
+  // material / contact constants (double and float copies)
+  double E, nu, rho, e_n, mu_s, mu_r, mu_t, eta, dt;
+  double g[3];
+  double beta;           // damping factor of e_n (Sec. 2.2)
+  double Es_pp, Gs_pp;   // effective moduli particle-particle (same material)
+  double Es_pw, Gs_pw;   // particle-wall limits
+  double mesh_omega[3], mesh_center[3];
+  double omega_norm;     // |mesh_omega|
+  double mesh_rmax;      // largest vertex distance from the rotation axis
+  // binning
+  double origin[3];      // shifted coordinates X = x - origin
+  double base[3];        // power-of-two offset: domain_lo - origin
+  float inv_h;           // 1 / cell edge
+  float h;
+  int32_t nc[3];         // cells per axis
+  int64_t ncells;
+  float skin;
+  float half_skin_trigger;  // skin/2 minus the float margin
+  float list_margin;        // conservative float margin of candidate tests
+  float rmax;               // largest particle radius
+  float mesh_prefilter;     // float margin before the FP64 triangle geometry (mixed)
+  float center_hi[3], center_lo[3];  // mesh_center - origin as hi/lo floats
+  int32_t n;
+  int32_t cap;              // pair-list capacity per particle
+  int32_t capm;             // triangle-candidate capacity per particle
+  int32_t n_tri;
+  int32_t record_forces;
+  int32_t mixed;
+};
+
+// Dynamic state, double precision: four 32-byte records per particle.
+struct StateD {
+  D4* P;  // x, y, z (absolute), R
+  D4* V;  // v, m
+  D4* W;  // w, unused
+  D4* Q;  // q0..q3
+};
+
+// Dynamic state, compensated single precision (hi + lo pairs).
+struct __align__(32) F8 {
+  float4 hi, lo;
+};
+struct StateM {
+  F8* P;  // X - origin (shifted, hi/lo), R (hi/lo)
+  F8* V;  // v (hi/lo); hi.w = m
+  F8* W;  // w (hi/lo)
+  F8* Q;  // q (hi/lo)
+};
+
+// Friction history of one contact, in the precision of the contact math.
+// stamp = 1 + index of the step that last wrote it; a record is carried into
+// step s only if stamp == s, i.e. the contact was touching in step s - 1.
+struct HistD {
+  double us[3];
+  double ur[3];
+  double ut;
+  uint32_t stamp;
+  uint32_t pad;
+};
+struct HistM {
+  float us[3];
+  float ur[3];
+  float ut;
+  uint32_t stamp;
+};
+static_assert(sizeof(HistD) == 64, "HistD must be 64 bytes");
+static_assert(sizeof(HistM) == 32, "HistM must be 32 bytes");
+
+constexpr uint32_t kStampNone = 0xffffffffu;
+
+// Lists and per-slot data valid between two rebuilds (double-buffered by lphase).
+struct ListBuf {
+  uint32_t* gid;    // [n] caller index of the particle in each slot
+  float4* posf;     // [n] shifted position (float) and radius at the rebuild
+  uint32_t* meta;   // [n] list length | lower-id count << 8 | triangle count << 16
+  uint32_t* nbr;    // [cap][n] partner slots, ascending partner caller index
+  uint32_t* tric;   // [capm][n] candidate triangles, ascending
+  void* hpp;        // [cap][n] pair history (HistD or HistM)
+  void* hpm;        // [capm][n] triangle history
+};
+
+// Mesh at the current pose.
+struct MeshDev {
+  D4* ref;      // [nv] reference vertices (x, y, z, 0)
+  int4* tri;         // [nt] vertex indices, w unused
+  double* rad;       // [nt] element radius
+  D4* cur;      // [nt][3] current triangle vertices (absolute), w of the first = radius
+  float4* curf;      // [nt][3] current vertices in shifted coordinates (float)
+  int32_t nv, nt;
+};
+
+// Binning scratch.
+struct BinBuf {
+  uint32_t* key;        // [n] cell of each slot (current order)
+  uint32_t* local;      // [n] arrival index within its cell
+  uint32_t* cell_count; // [ncells]
+  uint32_t* cell_start; // [ncells + 1]
+  uint32_t* order;      // [n] old slot of each new slot
+  uint32_t* block_sums; // scan partials
+  // triangle cell lists
+  uint32_t* tcell_count;  // [ncells]
+  uint32_t* tcell_start;  // [ncells + 1]
+  uint32_t* tcell_tri;    // [tcap]
+  uint32_t tcap;
+  uint32_t* tcell_overflow;
+};
+
+// Both parities of the double-buffered data.  Kernels pick the current one
+// from the control block (ctl->phase for the dynamic state, ctl->lphase for
+// lists and histories), so the launch sequence never depends on host state.
+// Record type: D4 (DEM_FP64) or F8 (DEM_MIXED).
+struct StateBufs {
+  void* P[2];
+  void* V[2];
+  void* W[2];
+  void* Q[2];
+};
+struct Lists {
+  ListBuf b[2];
+};
+
+// Kernel launch helpers implemented in the .cu files.
+void launch_mesh_pose(cudaStream_t st, const Ctl* ctl, const Params& p, MeshDev mesh);
+void launch_rebuild(cudaStream_t st, Ctl* ctl, const Params& p, StateBufs sb, Lists L,
+                    BinBuf bb, MeshDev mesh);
+void launch_step(cudaStream_t st, Ctl* ctl, const Params& p, StateBufs sb, Lists L,
+                 MeshDev mesh, double* forces);
+void launch_advance(cudaStream_t st, Ctl* ctl, const Params& p);
+
+// Scan of a u32 array (exclusive) on the device; early-exits unless ctl->rebuild.
+void launch_scan(cudaStream_t st, const Ctl* ctl, const uint32_t* in, uint32_t* out, int64_t n,
+                 uint32_t* block_sums);
+int64_t scan_block_sums_size(int64_t n);
+
+}  // namespace dem

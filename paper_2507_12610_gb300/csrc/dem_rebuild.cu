@@ -1,0 +1,396 @@
+// List rebuild: cell binning by counting sort, permutation of the particle
+// state into cell order, per-cell triangle lists, and the Verlet list build
+// with the pair-key history remap.
+//
+// The paper rebuilds a linked-cell list every step (Sec. 3.3); here cells are
+// only used to rebuild a Verlet list with skin (the extension of Sec. 7), and
+// the whole rebuild runs only in steps where the control block asks for it.
+// Every kernel returns at once otherwise, so a step is a fixed launch
+// sequence that a CUDA graph can replay.
+//
+// Determinism: particles are ordered by cell and, within a cell, by caller
+// index; lists are ordered by partner caller index; triangle lists by triangle
+// index.  Atomics are used only on integers (counts and arrival slots) whose
+// final values do not depend on thread order, and the within-cell sort removes
+// the arrival order.  The result depends only on positions.
+#include <algorithm>
+#include <cfloat>
+
+#include "dem_geom.cuh"
+#include "dem_internal.cuh"
+#include "dem_math.cuh"
+
+namespace dem {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ bool rebuilding(const Ctl* ctl) {
+  return ctl->rebuild != 0 && ctl->status == 0;
+}
+
+__device__ __forceinline__ void set_status(Ctl* ctl, uint32_t code) {
+  atomicCAS(&ctl->status, 0u, code);
+}
+
+// Shifted float position of slot s in the current dynamic state.
+__device__ __forceinline__ float4 posf_of(const Params& p, const void* state, uint32_t s) {
+  if (p.mixed) {
+    const F8 P = static_cast<const F8*>(state)[s];
+    return make_float4(P.hi.x + P.lo.x, P.hi.y + P.lo.y, P.hi.z + P.lo.z, P.hi.w + P.lo.w);
+  }
+  const D4 P = static_cast<const D4*>(state)[s];
+  return make_float4((float)(P.x - p.origin[0]), (float)(P.y - p.origin[1]),
+                     (float)(P.z - p.origin[2]), (float)P.w);
+}
+
+__global__ void k_clear(const Ctl* ctl, uint32_t* a, int64_t n) {
+  if (!rebuilding(ctl)) return;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    a[i] = 0u;
+}
+
+// key = cell of each particle; local = its arrival index in the cell.
+__global__ void __launch_bounds__(kThreads)
+k_bin_count(const Ctl* ctl, Params p, StateBufs sb, BinBuf bb) {
+  if (!rebuilding(ctl)) return;
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= p.n) return;
+  const float4 X = posf_of(p, sb.P[ctl->phase & 1u], s);
+  const uint32_t c = cell_index(p, cell_coords(p, X.x, X.y, X.z));
+  bb.key[s] = c;
+  bb.local[s] = atomicAdd(&bb.cell_count[c], 1u);
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_scatter(const Ctl* ctl, Params p, BinBuf bb) {
+  if (!rebuilding(ctl)) return;
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= p.n) return;
+  bb.order[bb.cell_start[bb.key[s]] + bb.local[s]] = (uint32_t)s;
+}
+
+// Within each cell, order the particles by caller index (insertion sort; a
+// cell holds a handful of particles).
+__global__ void __launch_bounds__(kThreads)
+k_cell_sort(const Ctl* ctl, Params p, BinBuf bb, Lists L) {
+  if (!rebuilding(ctl)) return;
+  const uint32_t* gid_old = L.b[ctl->lphase & 1u].gid;
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < p.ncells;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t a = bb.cell_start[c], b = bb.cell_start[c + 1];
+    for (uint32_t i = a + 1; i < b; ++i) {
+      const uint32_t v = bb.order[i];
+      const uint32_t gv = gid_old[v];
+      uint32_t j = i;
+      while (j > a && gid_old[bb.order[j - 1]] > gv) {
+        bb.order[j] = bb.order[j - 1];
+        --j;
+      }
+      bb.order[j] = v;
+    }
+  }
+}
+
+// Move the dynamic state and the per-slot identity into cell order.
+template <typename Rec>
+__global__ void __launch_bounds__(kThreads)
+k_permute(const Ctl* ctl, Params p, BinBuf bb, StateBufs sb, Lists L) {
+  if (!rebuilding(ctl)) return;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= p.n) return;
+  const uint32_t ph = ctl->phase & 1u, lph = ctl->lphase & 1u;
+  const Rec* P0 = static_cast<const Rec*>(sb.P[ph]);
+  const Rec* V0 = static_cast<const Rec*>(sb.V[ph]);
+  const Rec* W0 = static_cast<const Rec*>(sb.W[ph]);
+  const Rec* Q0 = static_cast<const Rec*>(sb.Q[ph]);
+  Rec* P1 = static_cast<Rec*>(sb.P[ph ^ 1u]);
+  Rec* V1 = static_cast<Rec*>(sb.V[ph ^ 1u]);
+  Rec* W1 = static_cast<Rec*>(sb.W[ph ^ 1u]);
+  Rec* Q1 = static_cast<Rec*>(sb.Q[ph ^ 1u]);
+  const uint32_t* gid_old = L.b[lph].gid;
+  uint32_t* gid_new = L.b[lph ^ 1u].gid;
+  float4* posf_new = L.b[lph ^ 1u].posf;
+  const uint32_t s = bb.order[t];
+  P1[t] = P0[s];
+  V1[t] = V0[s];
+  W1[t] = W0[s];
+  Q1[t] = Q0[s];
+  gid_new[t] = gid_old[s];
+  posf_new[t] = posf_of(p, P0, s);
+}
+
+// ---- triangle cell lists -----------------------------------------------------
+
+// Cells within reach of triangle k: its bounding box grown by the reach
+// R_k + R_max + skin (+ margin), then a conservative per-cell test: the cell
+// centre within reach + half the cell diagonal of the triangle.  pass 0
+// counts, pass 1 fills.  One block per triangle.
+__global__ void k_tri_cells(const Ctl* ctl, Params p, MeshDev mesh, BinBuf bb, int pass) {
+  if (!rebuilding(ctl)) return;
+  const int k = blockIdx.x;
+  if (k >= mesh.nt) return;
+  const float4 A = mesh.curf[3 * k], B = mesh.curf[3 * k + 1], C = mesh.curf[3 * k + 2];
+  const float reach = (float)mesh.rad[k] + p.rmax + p.skin + p.list_margin;
+  const float3 lo = make_float3(fminf(A.x, fminf(B.x, C.x)) - reach,
+                                fminf(A.y, fminf(B.y, C.y)) - reach,
+                                fminf(A.z, fminf(B.z, C.z)) - reach);
+  const float3 hi = make_float3(fmaxf(A.x, fmaxf(B.x, C.x)) + reach,
+                                fmaxf(A.y, fmaxf(B.y, C.y)) + reach,
+                                fmaxf(A.z, fmaxf(B.z, C.z)) + reach);
+  const int3 c0 = cell_coords(p, lo.x, lo.y, lo.z);
+  const int3 c1 = cell_coords(p, hi.x, hi.y, hi.z);
+  const int nx = c1.x - c0.x + 1, ny = c1.y - c0.y + 1, nz = c1.z - c0.z + 1;
+  const int64_t total = (int64_t)nx * ny * nz;
+  const float halfdiag = 0.5f * p.h * 1.7320508f * 1.0001f;
+  const float lim = reach + halfdiag;
+  const V3<float> a = mk(A.x, A.y, A.z), b = mk(B.x, B.y, B.z), c = mk(C.x, C.y, C.z);
+  for (int64_t i = threadIdx.x; i < total; i += blockDim.x) {
+    const int cx = c0.x + (int)(i % nx);
+    const int cy = c0.y + (int)((i / nx) % ny);
+    const int cz = c0.z + (int)(i / ((int64_t)nx * ny));
+    const V3<float> q = mk((float)p.base[0] + (cx + 0.5f) * p.h,
+                           (float)p.base[1] + (cy + 0.5f) * p.h,
+                           (float)p.base[2] + (cz + 0.5f) * p.h);
+    // boundary cells also hold clamped particles from outside the box:
+    // accept them whenever the triangle is within reach of the clamped region
+    const bool edge = cx == 0 || cy == 0 || cz == 0 || cx == p.nc[0] - 1 ||
+                      cy == p.nc[1] - 1 || cz == p.nc[2] - 1;
+    bool hit = edge;
+    if (!hit) {
+      const V3<float> y = closest_point_triangle(q, a, b, c);
+      const V3<float> d = q - y;
+      hit = dot(d, d) <= lim * lim;
+    }
+    if (!hit) continue;
+    const uint32_t cell = (uint32_t)((cz * p.nc[1] + cy) * p.nc[0] + cx);
+    if (pass == 0) {
+      atomicAdd(&bb.tcell_count[cell], 1u);
+    } else {
+      const uint32_t pos = bb.tcell_start[cell] + atomicAdd(&bb.tcell_count[cell], 1u);
+      if (pos < bb.tcap) bb.tcell_tri[pos] = (uint32_t)k;
+    }
+  }
+}
+
+__global__ void k_tri_cells_check(Ctl* ctl, Params p, BinBuf bb) {
+  if (!rebuilding(ctl)) return;
+  if (bb.tcell_start[p.ncells] > bb.tcap) {
+    *bb.tcell_overflow = bb.tcell_start[p.ncells];
+    set_status(ctl, DEM_ERR_CAPACITY);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_tri_cell_sort(const Ctl* ctl, Params p, BinBuf bb) {
+  if (!rebuilding(ctl)) return;
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < p.ncells;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t a = bb.tcell_start[c], b = bb.tcell_start[c + 1];
+    for (uint32_t i = a + 1; i < b; ++i) {
+      const uint32_t v = bb.tcell_tri[i];
+      uint32_t j = i;
+      while (j > a && bb.tcell_tri[j - 1] > v) {
+        bb.tcell_tri[j] = bb.tcell_tri[j - 1];
+        --j;
+      }
+      bb.tcell_tri[j] = v;
+    }
+  }
+}
+
+// ---- Verlet list build + history remap -----------------------------------------
+
+template <typename Hist>
+__device__ __forceinline__ void mark_empty(Hist* h) {
+  h->stamp = kStampNone;
+}
+
+// For one new slot t: collect the partners within R_t + R_u + skin (float test
+// with a conservative margin) from the 27 surrounding cells, sort them by
+// caller index, write the list, and carry each pair's friction history over
+// from the particle's previous list (merge of two lists sorted by caller
+// index; a history is kept only if the contact touched in the previous step).
+// Then the same for triangle candidates from the particle's cell.
+template <typename Hist>
+__global__ void __launch_bounds__(128)
+k_list_build(Ctl* ctl, Params p, BinBuf bb, Lists L, MeshDev mesh) {
+  if (!rebuilding(ctl)) return;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= p.n) return;
+  const ListBuf lo = L.b[ctl->lphase & 1u];
+  const ListBuf ln = L.b[(ctl->lphase & 1u) ^ 1u];
+  const int n = p.n;
+  const float4 X = ln.posf[t];
+  const uint32_t gt = ln.gid[t];
+  const int3 c = cell_coords(p, X.x, X.y, X.z);
+
+  uint32_t cand_g[64];
+  uint32_t cand_s[64];
+  const int cap = min(p.cap, 64);
+  int cnt = 0;
+  bool overflow = false;
+  for (int dz = -1; dz <= 1; ++dz) {
+    const int cz = c.z + dz;
+    if (cz < 0 || cz >= p.nc[2]) continue;
+    for (int dy = -1; dy <= 1; ++dy) {
+      const int cy = c.y + dy;
+      if (cy < 0 || cy >= p.nc[1]) continue;
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int cx = c.x + dx;
+        if (cx < 0 || cx >= p.nc[0]) continue;
+        const uint32_t cell = (uint32_t)((cz * p.nc[1] + cy) * p.nc[0] + cx);
+        const uint32_t a = bb.cell_start[cell], b = bb.cell_start[cell + 1];
+        for (uint32_t u = a; u < b; ++u) {
+          if (u == (uint32_t)t) continue;
+          const float4 Y = ln.posf[u];
+          const float ddx = X.x - Y.x, ddy = X.y - Y.y, ddz = X.z - Y.z;
+          const float cut = X.w + Y.w + p.skin + p.list_margin;
+          if (ddx * ddx + ddy * ddy + ddz * ddz < cut * cut) {
+            if (cnt < cap) {
+              // insertion into the sorted candidate array
+              const uint32_t g = ln.gid[u];
+              int j = cnt;
+              while (j > 0 && cand_g[j - 1] > g) {
+                cand_g[j] = cand_g[j - 1];
+                cand_s[j] = cand_s[j - 1];
+                --j;
+              }
+              cand_g[j] = g;
+              cand_s[j] = u;
+              ++cnt;
+            } else {
+              overflow = true;
+            }
+          }
+        }
+      }
+    }
+  }
+  if (overflow) set_status(ctl, DEM_ERR_CAPACITY);
+
+  // old list of the same particle
+  const uint32_t s = bb.order[t];
+  const uint32_t mo = lo.meta[s];
+  const int nn_o = (int)(mo & 0xffu), nt_o = (int)((mo >> 16) & 0xffu);
+  const Hist* hpp_o = static_cast<const Hist*>(lo.hpp);
+  Hist* hpp_n = static_cast<Hist*>(ln.hpp);
+  const uint32_t stamp_now = (uint32_t)ctl->step;  // records written in the previous step
+  int nlow = 0;
+  int ko = 0;
+  uint32_t go = ko < nn_o ? lo.gid[lo.nbr[(size_t)ko * n + s]] : 0xffffffffu;
+  for (int k = 0; k < cnt; ++k) {
+    const uint32_t g = cand_g[k];
+    if (g < gt) ++nlow;
+    ln.nbr[(size_t)k * n + t] = cand_s[k];
+    while (ko < nn_o && go < g) {
+      ++ko;
+      go = ko < nn_o ? lo.gid[lo.nbr[(size_t)ko * n + s]] : 0xffffffffu;
+    }
+    Hist* dst = &hpp_n[(size_t)k * n + t];
+    if (ko < nn_o && go == g) {
+      const Hist h = hpp_o[(size_t)ko * n + s];
+      if (h.stamp == stamp_now) *dst = h;
+      else mark_empty(dst);
+    } else {
+      mark_empty(dst);
+    }
+  }
+
+  // triangle candidates
+  int ntc = 0;
+  if (mesh.nt > 0) {
+    const uint32_t cell = cell_index(p, c);
+    const uint32_t a = bb.tcell_start[cell], b = min(bb.tcell_start[cell + 1], bb.tcap);
+    const Hist* hpm_o = static_cast<const Hist*>(lo.hpm);
+    Hist* hpm_n = static_cast<Hist*>(ln.hpm);
+    int ko2 = 0;
+    const V3<float> q = mk(X.x, X.y, X.z);
+    bool tover = false;
+    for (uint32_t i = a; i < b; ++i) {
+      const uint32_t k = bb.tcell_tri[i];
+      const float4 A = mesh.curf[3 * k], B = mesh.curf[3 * k + 1], C = mesh.curf[3 * k + 2];
+      const V3<float> y = closest_point_triangle(q, mk(A.x, A.y, A.z), mk(B.x, B.y, B.z),
+                                                 mk(C.x, C.y, C.z));
+      const V3<float> d = q - y;
+      const float cut = X.w + (float)mesh.rad[k] + p.skin + p.list_margin;
+      if (dot(d, d) >= cut * cut) continue;
+      if (ntc >= p.capm) {
+        tover = true;
+        continue;
+      }
+      ln.tric[(size_t)ntc * n + t] = k;
+      while (ko2 < nt_o && lo.tric[(size_t)ko2 * n + s] < k) ++ko2;
+      Hist* dst = &hpm_n[(size_t)ntc * n + t];
+      if (ko2 < nt_o && lo.tric[(size_t)ko2 * n + s] == k) {
+        const Hist h = hpm_o[(size_t)ko2 * n + s];
+        if (h.stamp == stamp_now) *dst = h;
+        else mark_empty(dst);
+      } else {
+        mark_empty(dst);
+      }
+      ++ntc;
+    }
+    if (tover) set_status(ctl, DEM_ERR_CAPACITY);
+  }
+  ln.meta[t] = (uint32_t)cnt | ((uint32_t)nlow << 8) | ((uint32_t)ntc << 16);
+  atomicAdd(&ctl->list_entries, (uint32_t)cnt);
+  atomicAdd(&ctl->mesh_candidates, (uint32_t)ntc);
+  atomicMax(&ctl->max_list_len, (uint32_t)cnt);
+}
+
+__global__ void k_rebuild_prep(Ctl* ctl) {
+  if (!rebuilding(ctl)) return;
+  ctl->list_entries = 0;
+  ctl->mesh_candidates = 0;
+  ctl->max_list_len = 0;
+}
+
+__global__ void k_rebuild_end(Ctl* ctl, Params p) {
+  if (!rebuilding(ctl)) return;
+  ctl->phase ^= 1u;
+  ctl->lphase ^= 1u;
+  ctl->rebuilds += 1;
+  ctl->mesh_angle_ref = p.omega_norm * ((double)ctl->step * p.dt);
+}
+
+inline unsigned blocks_for(int64_t n, int threads) {
+  return (unsigned)((n + threads - 1) / threads);
+}
+
+}  // namespace
+
+void launch_rebuild(cudaStream_t st, Ctl* ctl, const Params& p, StateBufs sb, Lists L,
+                    BinBuf bb, MeshDev mesh) {
+  const unsigned nb = blocks_for(p.n, kThreads);
+  const unsigned gcells = (unsigned)std::min<int64_t>(blocks_for(p.ncells, kThreads), 152 * 16);
+  k_rebuild_prep<<<1, 1, 0, st>>>(ctl);
+  k_clear<<<gcells, kThreads, 0, st>>>(ctl, bb.cell_count, p.ncells);
+  k_bin_count<<<nb, kThreads, 0, st>>>(ctl, p, sb, bb);
+  launch_scan(st, ctl, bb.cell_count, bb.cell_start, p.ncells, bb.block_sums);
+  k_scatter<<<nb, kThreads, 0, st>>>(ctl, p, bb);
+  k_cell_sort<<<gcells, kThreads, 0, st>>>(ctl, p, bb, L);
+  if (p.mixed)
+    k_permute<F8><<<nb, kThreads, 0, st>>>(ctl, p, bb, sb, L);
+  else
+    k_permute<D4><<<nb, kThreads, 0, st>>>(ctl, p, bb, sb, L);
+  if (mesh.nt > 0) {
+    k_clear<<<gcells, kThreads, 0, st>>>(ctl, bb.tcell_count, p.ncells);
+    k_tri_cells<<<(unsigned)mesh.nt, 128, 0, st>>>(ctl, p, mesh, bb, 0);
+    launch_scan(st, ctl, bb.tcell_count, bb.tcell_start, p.ncells, bb.block_sums);
+    k_tri_cells_check<<<1, 1, 0, st>>>(ctl, p, bb);
+    k_clear<<<gcells, kThreads, 0, st>>>(ctl, bb.tcell_count, p.ncells);
+    k_tri_cells<<<(unsigned)mesh.nt, 128, 0, st>>>(ctl, p, mesh, bb, 1);
+    k_tri_cell_sort<<<gcells, kThreads, 0, st>>>(ctl, p, bb);
+  }
+  const unsigned nb128 = blocks_for(p.n, 128);
+  if (p.mixed)
+    k_list_build<HistM><<<nb128, 128, 0, st>>>(ctl, p, bb, L, mesh);
+  else
+    k_list_build<HistD><<<nb128, 128, 0, st>>>(ctl, p, bb, L, mesh);
+  k_rebuild_end<<<1, 1, 0, st>>>(ctl, p);
+}
+
+}  // namespace dem

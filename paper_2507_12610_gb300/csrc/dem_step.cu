@@ -1,0 +1,358 @@
+// One DEM time step on the device: mesh pose, contact forces from the Verlet
+// list (particle pairs and particle-triangle candidates), the per-particle
+// force/torque gather, and the semi-implicit Euler + SPIRAL integration
+// (arXiv 2507.12610, Sec. 2.1-2.3).
+//
+// One thread per particle slot.  A thread walks its list in ascending partner
+// caller index, then its triangle candidates in ascending triangle index, and
+// sums the contributions in exactly that order: the result is deterministic
+// and independent of the launch shape, the skin and the rebuild schedule (no
+// floating-point atomics anywhere).  Each touching pair is evaluated by both
+// of its particles in the canonical orientation (lower caller index = body i),
+// which gives both the same bits; each keeps its own copy of the friction
+// history, so no thread ever reads what another thread writes in this step.
+// Reading the old state and writing the new one to the other buffer keeps all
+// contacts of a step at the state of t_n (as in the paper's loop).
+#include "dem_geom.cuh"
+#include "dem_internal.cuh"
+#include "dem_law.cuh"
+#include "dem_math.cuh"
+#include "dem_step_common.cuh"
+
+namespace dem {
+
+namespace {
+
+// ---- mesh pose: reference vertices rotated by |Omega| t about the axis ------
+
+__global__ void k_mesh_pose(const Ctl* ctl, Params p, MeshDev mesh) {
+  if (ctl->status) return;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= mesh.nt) return;
+  const double wn = p.omega_norm;
+  double c = 1.0, s = 0.0;
+  V3<double> ax = mk(0.0, 0.0, 0.0);
+  const V3<double> ctr = mk(p.mesh_center[0], p.mesh_center[1], p.mesh_center[2]);
+  if (wn > 0.0) {
+    const double th = wn * ((double)ctl->step * p.dt);
+    c = cos(th);
+    s = sin(th);
+    ax = (1.0 / wn) * mk(p.mesh_omega[0], p.mesh_omega[1], p.mesh_omega[2]);
+  }
+  const int4 tv = mesh.tri[k];
+  const int idx[3] = {tv.x, tv.y, tv.z};
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const D4 r0 = mesh.ref[idx[j]];
+    V3<double> pos = xyz(r0);
+    if (wn > 0.0) {
+      const V3<double> r = pos - ctr;
+      const V3<double> rr = c * r + s * cross(ax, r) + (dot(ax, r) * (1.0 - c)) * ax;
+      pos = ctr + rr;
+    }
+    mesh.cur[3 * k + j] = make_D4(pos.x, pos.y, pos.z, j == 0 ? mesh.rad[k] : 0.0);
+    mesh.curf[3 * k + j] = make_float4((float)(pos.x - p.origin[0]), (float)(pos.y - p.origin[1]),
+                                       (float)(pos.z - p.origin[2]), 0.f);
+  }
+}
+
+// ---- end of step: flip buffers, count, decide the next rebuild -------------
+
+__global__ void k_advance(Ctl* ctl, Params p) {
+  if (ctl->status) return;
+  ctl->phase ^= 1u;
+  ctl->step += 1;
+  ctl->pair_contacts_last = ctl->pair_contacts;
+  ctl->mesh_contacts_last = ctl->mesh_contacts;
+  ctl->pair_contacts = 0;
+  ctl->mesh_contacts = 0;
+  // mesh displacement since the last rebuild: a point at distance r from the
+  // axis moves by the chord 2 r |sin(dtheta / 2)|
+  bool mesh_moved = false;
+  if (p.omega_norm > 0.0) {
+    const double th = p.omega_norm * ((double)ctl->step * p.dt);
+    const double chord = 2.0 * p.mesh_rmax * fabs(sin(0.5 * (th - ctl->mesh_angle_ref)));
+    mesh_moved = chord >= (double)p.half_skin_trigger;
+  }
+  ctl->rebuild = (ctl->disp_flag || ctl->force_rebuild || mesh_moved) ? 1u : 0u;
+  ctl->disp_flag = 0u;
+  ctl->force_rebuild = 0u;
+}
+
+// ============================================================================
+// DEM_MIXED: contact arithmetic in FP32, state as compensated hi/lo pairs
+// ============================================================================
+
+__device__ __forceinline__ V3<float> hi3(float4 a) { return mk(a.x, a.y, a.z); }
+// accurate difference of two hi/lo 3-vectors, rounded once
+__device__ __forceinline__ V3<float> diff3(const F8& a, const F8& b) {
+  return mk((a.hi.x - b.hi.x) + (a.lo.x - b.lo.x), (a.hi.y - b.hi.y) + (a.lo.y - b.lo.y),
+            (a.hi.z - b.hi.z) + (a.lo.z - b.lo.z));
+}
+__device__ __forceinline__ V3<float> sum3(const F8& a) {
+  return mk(a.hi.x + a.lo.x, a.hi.y + a.lo.y, a.hi.z + a.lo.z);
+}
+// (hi, lo) + b, renormalised
+__device__ __forceinline__ void acc(float& hi, float& lo, float b) {
+  const ff s = ff_add_f(ff{hi, lo}, b);
+  hi = s.hi;
+  lo = s.lo;
+}
+
+__global__ void __launch_bounds__(128)
+k_step_mixed(Ctl* ctl, Params p, StateBufs sb, Lists L, MeshDev mesh, double* forces) {
+  if (ctl->status) return;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = p.n;
+  const uint32_t ph = ctl->phase & 1u, lph = ctl->lphase & 1u;
+  const uint32_t stamp_now = (uint32_t)ctl->step;
+  const uint32_t stamp_new = stamp_now + 1u;
+  uint32_t npair = 0, nmesh = 0;
+  bool disp = false, bad = false;
+  if (t < n) {
+    const F8* P = static_cast<const F8*>(sb.P[ph]);
+    const F8* V = static_cast<const F8*>(sb.V[ph]);
+    const F8* W = static_cast<const F8*>(sb.W[ph]);
+    const F8* Q = static_cast<const F8*>(sb.Q[ph]);
+    const ListBuf lb = L.b[lph];
+    const F8 Pt = P[t], Vt = V[t], Wt = W[t];
+    const uint32_t meta = lb.meta[t];
+    const int nn = (int)(meta & 0xffu), nlow = (int)((meta >> 8) & 0xffu),
+              ntc = (int)((meta >> 16) & 0xffu);
+    const LawConst<float> cpp{(float)p.Es_pp, (float)p.Gs_pp, (float)p.beta, (float)p.mu_s,
+                              (float)p.mu_r, (float)p.mu_t, (float)p.dt};
+    Acc3 F, T;
+    F.zero();
+    T.zero();
+    HistM* hpp = static_cast<HistM*>(lb.hpp);
+    const float Rt = Pt.hi.w + Pt.lo.w;
+    for (int k = 0; k < nn; ++k) {
+      const uint32_t u = lb.nbr[(size_t)k * n + t];
+      const F8 Pu = P[u];
+      const bool t_is_i = k >= nlow;
+      const F8 Pi = t_is_i ? Pt : Pu, Pj = t_is_i ? Pu : Pt;
+      // centre distance: hi parts share a binade (shifted coordinates), so
+      // their difference is exact; the lo parts add the remaining bits
+      const float dxh = Pi.hi.x - Pj.hi.x, dyh = Pi.hi.y - Pj.hi.y, dzh = Pi.hi.z - Pj.hi.z;
+      const float dxl = Pi.lo.x - Pj.lo.x, dyl = Pi.lo.y - Pj.lo.y, dzl = Pi.lo.z - Pj.lo.z;
+      const V3<float> dq = mk(dxh + dxl, dyh + dyl, dzh + dzl);
+      const float Sf = (Pi.hi.w + Pi.lo.w) + (Pj.hi.w + Pj.lo.w);
+      const float d2f = dot(dq, dq);
+      if (d2f > Sf * Sf * 1.0001f) continue;  // clearly apart
+      // overlap delta = (S^2 - d^2) / (S + d) in compensated arithmetic
+      ff sx = two_prod(dxh, dxh);
+      sx.lo = __fmaf_rn(2.f * dxh, dxl, sx.lo);
+      ff sy = two_prod(dyh, dyh);
+      sy.lo = __fmaf_rn(2.f * dyh, dyl, sy.lo);
+      ff sz = two_prod(dzh, dzh);
+      sz.lo = __fmaf_rn(2.f * dzh, dzl, sz.lo);
+      const ff d2 = ff_add(ff_add(sx, sy), sz);
+      ff S = two_sum(Pi.hi.w, Pj.hi.w);
+      S.lo += Pi.lo.w + Pj.lo.w;
+      S = fast_two_sum(S.hi, S.lo);
+      ff S2 = two_prod(S.hi, S.hi);
+      S2.lo = __fmaf_rn(2.f * S.hi, S.lo, S2.lo);
+      const ff df = ff_add(S2, ff_neg(d2));
+      const float num = df.hi + df.lo;
+      if (num < 0.f) continue;
+      const float dist = sqrtf(d2.hi + d2.lo);
+      if (!(dist > 0.f)) continue;
+      const float delta = num / ((S.hi + S.lo) + dist);
+      const F8 Vu = V[u], Wu = W[u];
+      const F8 Vi = t_is_i ? Vt : Vu, Vj = t_is_i ? Vu : Vt;
+      const F8 Wi = t_is_i ? Wt : Wu, Wj = t_is_i ? Wu : Wt;
+      const float idist = 1.f / dist;
+      const V3<float> nh = idist * dq;
+      const float Ri = Pi.hi.w + Pi.lo.w, Rj = Pj.hi.w + Pj.lo.w;
+      const float Rs = 1.f / (1.f / Ri + 1.f / Rj);
+      const float ms = 1.f / (1.f / Vi.hi.w + 1.f / Vj.hi.w);
+      const float ri = Ri - 0.5f * delta, rj = Rj - 0.5f * delta;
+      HistM* hp = &hpp[(size_t)k * n + t];
+      const HistM h = *hp;
+      V3<float> us = mk(0.f, 0.f, 0.f), ur = us;
+      float ut = 0.f;
+      if (h.stamp == stamp_now) {
+        us = mk(h.us[0], h.us[1], h.us[2]);
+        ur = mk(h.ur[0], h.ur[1], h.ur[2]);
+        ut = h.ut;
+      }
+      const LawOut<float> o =
+          contact_law(cpp, nh, delta, Rs, ms, ri, rj, 1.f / ri + 1.f / rj, diff3(Vi, Vj),
+                      ri * sum3(Wi) + rj * sum3(Wj), diff3(Wi, Wj), us, ur, ut);
+      HistM hn;
+      hn.us[0] = us.x; hn.us[1] = us.y; hn.us[2] = us.z;
+      hn.ur[0] = ur.x; hn.ur[1] = ur.y; hn.ur[2] = ur.z;
+      hn.ut = ut;
+      hn.stamp = stamp_new;
+      *hp = hn;
+      if (t_is_i) {
+        F.add(o.f);
+        T.add(o.ti);
+      } else {
+        F.add(-o.f);
+        T.add(o.tj);
+      }
+      ++npair;
+    }
+    // particle-triangle contacts: float pre-filter, then the geometry of the
+    // near candidates in FP64 (a triangle is large compared with the overlap)
+    if (ntc > 0) {
+      const LawConst<float> cpw{(float)p.Es_pw, (float)p.Gs_pw, (float)p.beta, (float)p.mu_s,
+                                (float)p.mu_r, (float)p.mu_t, (float)p.dt};
+      HistM* hpm = static_cast<HistM*>(lb.hpm);
+      const V3<float> qf = sum3(Pt);
+      const V3<double> xd = mk(p.origin[0] + ((double)Pt.hi.x + (double)Pt.lo.x),
+                               p.origin[1] + ((double)Pt.hi.y + (double)Pt.lo.y),
+                               p.origin[2] + ((double)Pt.hi.z + (double)Pt.lo.z));
+      const V3<float> Om = mk((float)p.mesh_omega[0], (float)p.mesh_omega[1],
+                              (float)p.mesh_omega[2]);
+      // particle centre relative to the rotation axis point, accurately
+      const V3<float> rc = mk((Pt.hi.x - p.center_hi[0]) + (Pt.lo.x - p.center_lo[0]),
+                              (Pt.hi.y - p.center_hi[1]) + (Pt.lo.y - p.center_lo[1]),
+                              (Pt.hi.z - p.center_hi[2]) + (Pt.lo.z - p.center_lo[2]));
+      for (int m = 0; m < ntc; ++m) {
+        const uint32_t kt = lb.tric[(size_t)m * n + t];
+        const float4 Af = mesh.curf[3 * kt], Bf = mesh.curf[3 * kt + 1], Cf = mesh.curf[3 * kt + 2];
+        const V3<float> yf = closest_point_triangle(qf, hi3(Af), hi3(Bf), hi3(Cf));
+        const V3<float> df = qf - yf;
+        const D4 A = mesh.cur[3 * kt];
+        const float reachf = Rt + (float)A.w + p.mesh_prefilter;
+        if (dot(df, df) > reachf * reachf) continue;
+        const D4 B = mesh.cur[3 * kt + 1], C = mesh.cur[3 * kt + 2];
+        const V3<double> pc = closest_point_triangle(xd, xyz(A), xyz(B), xyz(C));
+        const V3<double> dd = xd - pc;
+        const double distd = sqrt(dot(dd, dd));
+        const double deltad = ((double)Pt.hi.w + (double)Pt.lo.w) + A.w - distd;
+        if (deltad < 0.0 || !(distd > 0.0)) continue;
+        const float delta = (float)deltad;
+        const double idd = 1.0 / distd;
+        const V3<float> nh = mk((float)(dd.x * idd), (float)(dd.y * idd), (float)(dd.z * idd));
+        const float ri = Rt - 0.5f * delta;
+        const V3<float> vw = cross(Om, rc - ri * nh);
+        HistM* hp = &hpm[(size_t)m * n + t];
+        const HistM h = *hp;
+        V3<float> us = mk(0.f, 0.f, 0.f), ur = us;
+        float ut = 0.f;
+        if (h.stamp == stamp_now) {
+          us = mk(h.us[0], h.us[1], h.us[2]);
+          ur = mk(h.ur[0], h.ur[1], h.ur[2]);
+          ut = h.ut;
+        }
+        const V3<float> dv = mk((Vt.hi.x - vw.x) + Vt.lo.x, (Vt.hi.y - vw.y) + Vt.lo.y,
+                                (Vt.hi.z - vw.z) + Vt.lo.z);
+        const V3<float> om = mk((Wt.hi.x - Om.x) + Wt.lo.x, (Wt.hi.y - Om.y) + Wt.lo.y,
+                                (Wt.hi.z - Om.z) + Wt.lo.z);
+        const LawOut<float> o = contact_law(cpw, nh, delta, Rt, Vt.hi.w, ri, 0.f, 1.f / ri, dv,
+                                            ri * sum3(Wt), om, us, ur, ut);
+        HistM hn;
+        hn.us[0] = us.x; hn.us[1] = us.y; hn.us[2] = us.z;
+        hn.ur[0] = ur.x; hn.ur[1] = ur.y; hn.ur[2] = ur.z;
+        hn.ut = ut;
+        hn.stamp = stamp_new;
+        *hp = hn;
+        F.add(o.f);
+        T.add(o.ti);
+        ++nmesh;
+      }
+    }
+    // semi-implicit Euler + SPIRAL with compensated (hi, lo) state
+    const float mass = Vt.hi.w;
+    const float R = Rt;
+    const float I = 0.4f * mass * R * R;
+    const float ci = (float)(9.0 * p.eta / (2.0 * p.rho)) / (R * R);
+    const float gi = 10.f / 3.f * ci;
+    const float dt = (float)p.dt;
+    const V3<float> v0 = sum3(Vt), w0 = sum3(Wt);
+    const float im = 1.f / mass, iI = 1.f / I;
+    const V3<float> a = mk((F.hx + F.lx) * im + (float)p.g[0] - ci * v0.x,
+                           (F.hy + F.ly) * im + (float)p.g[1] - ci * v0.y,
+                           (F.hz + F.lz) * im + (float)p.g[2] - ci * v0.z);
+    const V3<float> al = mk((T.hx + T.lx) * iI - gi * w0.x, (T.hy + T.ly) * iI - gi * w0.y,
+                            (T.hz + T.lz) * iI - gi * w0.z);
+    F8 Vn = Vt, Pn = Pt, Wn = Wt, Qn = Q[t];
+    acc(Vn.hi.x, Vn.lo.x, dt * a.x);
+    acc(Vn.hi.y, Vn.lo.y, dt * a.y);
+    acc(Vn.hi.z, Vn.lo.z, dt * a.z);
+    acc(Pn.hi.x, Pn.lo.x, dt * Vn.hi.x + dt * Vn.lo.x);
+    acc(Pn.hi.y, Pn.lo.y, dt * Vn.hi.y + dt * Vn.lo.y);
+    acc(Pn.hi.z, Pn.lo.z, dt * Vn.hi.z + dt * Vn.lo.z);
+    // orientation: q <- q (cos phi, sin phi w^) (cos th, sin th al^), applied as
+    // q + q (cos - 1, sin axis) so the small increment is formed in FP32 and
+    // added to the compensated quaternion
+    const float wn = sqrtf(dot(w0, w0));
+    if (wn > 0.f) {
+      const float phi = 0.5f * dt * wn;
+      const float sh = sinf(0.5f * phi);
+      const float sp = sinf(phi);
+      const float r[4] = {-2.f * sh * sh, sp * w0.x / wn, sp * w0.y / wn, sp * w0.z / wn};
+      const float qh[4] = {Qn.hi.x + Qn.lo.x, Qn.hi.y + Qn.lo.y, Qn.hi.z + Qn.lo.z,
+                           Qn.hi.w + Qn.lo.w};
+      float dq[4];
+      qmul(qh, r, dq);
+      acc(Qn.hi.x, Qn.lo.x, dq[0]);
+      acc(Qn.hi.y, Qn.lo.y, dq[1]);
+      acc(Qn.hi.z, Qn.lo.z, dq[2]);
+      acc(Qn.hi.w, Qn.lo.w, dq[3]);
+    }
+    const float an = sqrtf(dot(al, al));
+    if (an > 0.f) {
+      const float th = (0.5f * dt) * (0.5f * dt) * an;
+      const float sh = sinf(0.5f * th);
+      const float st = sinf(th);
+      const float r[4] = {-2.f * sh * sh, st * al.x / an, st * al.y / an, st * al.z / an};
+      const float qh[4] = {Qn.hi.x + Qn.lo.x, Qn.hi.y + Qn.lo.y, Qn.hi.z + Qn.lo.z,
+                           Qn.hi.w + Qn.lo.w};
+      float dq[4];
+      qmul(qh, r, dq);
+      acc(Qn.hi.x, Qn.lo.x, dq[0]);
+      acc(Qn.hi.y, Qn.lo.y, dq[1]);
+      acc(Qn.hi.z, Qn.lo.z, dq[2]);
+      acc(Qn.hi.w, Qn.lo.w, dq[3]);
+    }
+    acc(Wn.hi.x, Wn.lo.x, dt * al.x);
+    acc(Wn.hi.y, Wn.lo.y, dt * al.y);
+    acc(Wn.hi.z, Wn.lo.z, dt * al.z);
+    static_cast<F8*>(sb.P[ph ^ 1u])[t] = Pn;
+    static_cast<F8*>(sb.V[ph ^ 1u])[t] = Vn;
+    static_cast<F8*>(sb.W[ph ^ 1u])[t] = Wn;
+    static_cast<F8*>(sb.Q[ph ^ 1u])[t] = Qn;
+    if (p.record_forces) {
+      double* fo = forces + 6 * (size_t)t;
+      fo[0] = (double)F.hx + (double)F.lx;
+      fo[1] = (double)F.hy + (double)F.ly;
+      fo[2] = (double)F.hz + (double)F.lz;
+      fo[3] = (double)T.hx + (double)T.lx;
+      fo[4] = (double)T.hy + (double)T.ly;
+      fo[5] = (double)T.hz + (double)T.lz;
+    }
+    bad = !isfinite(Pn.hi.x + Pn.hi.y + Pn.hi.z + Vn.hi.x + Vn.hi.y + Vn.hi.z + Wn.hi.x +
+                    Wn.hi.y + Wn.hi.z);
+    const float4 pr = lb.posf[t];
+    const float ex = (Pn.hi.x - pr.x) + Pn.lo.x, ey = (Pn.hi.y - pr.y) + Pn.lo.y,
+                ez = (Pn.hi.z - pr.z) + Pn.lo.z;
+    disp = ex * ex + ey * ey + ez * ez >= p.half_skin_trigger * p.half_skin_trigger;
+  }
+  count_and_flag(ctl, npair, nmesh, disp, bad);
+}
+
+}  // namespace
+
+void launch_mesh_pose(cudaStream_t st, const Ctl* ctl, const Params& p, MeshDev mesh) {
+  if (mesh.nt <= 0) return;
+  k_mesh_pose<<<(unsigned)((mesh.nt + 127) / 128), 128, 0, st>>>(ctl, p, mesh);
+}
+
+void launch_step(cudaStream_t st, Ctl* ctl, const Params& p, StateBufs sb, Lists L,
+                 MeshDev mesh, double* forces) {
+  const unsigned nb = (unsigned)((p.n + 127) / 128);
+  if (p.mixed)
+    k_step_mixed<<<nb, 128, 0, st>>>(ctl, p, sb, L, mesh, forces);
+  else
+    launch_step_fp64(st, ctl, p, sb, L, mesh, forces);
+}
+
+void launch_advance(cudaStream_t st, Ctl* ctl, const Params& p) {
+  k_advance<<<1, 1, 0, st>>>(ctl, p);
+}
+
+}  // namespace dem

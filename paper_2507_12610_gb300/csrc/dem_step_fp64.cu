@@ -1,0 +1,197 @@
+// DEM_FP64 step kernel: contact forces, gather and integration in IEEE double
+// precision (arXiv 2507.12610, Sec. 2.1-2.3).  This translation unit is
+// compiled without floating-point contraction (--fmad=false), so every product
+// and sum is rounded as written, as in a plain double-precision program; the
+// kernel is the precision reference of the library.  The structure is the one
+// described in dem_step.cu: one thread per particle slot, partners in
+// ascending caller index, canonical pair orientation, no atomics on floats.
+#include "dem_geom.cuh"
+#include "dem_internal.cuh"
+#include "dem_law.cuh"
+#include "dem_math.cuh"
+#include "dem_step_common.cuh"
+
+namespace dem {
+
+namespace {
+
+// ============================================================================
+// DEM_FP64
+// ============================================================================
+
+__global__ void __launch_bounds__(128)
+k_step_fp64(Ctl* ctl, Params p, StateBufs sb, Lists L, MeshDev mesh, double* forces) {
+  if (ctl->status) return;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = p.n;
+  const uint32_t ph = ctl->phase & 1u, lph = ctl->lphase & 1u;
+  const uint32_t stamp_now = (uint32_t)ctl->step;
+  const uint32_t stamp_new = stamp_now + 1u;
+  uint32_t npair = 0, nmesh = 0;
+  bool disp = false, bad = false;
+  if (t < n) {
+    const D4* P = static_cast<const D4*>(sb.P[ph]);
+    const D4* V = static_cast<const D4*>(sb.V[ph]);
+    const D4* W = static_cast<const D4*>(sb.W[ph]);
+    const D4* Q = static_cast<const D4*>(sb.Q[ph]);
+    const ListBuf lb = L.b[lph];
+    const D4 Pt = P[t], Vt = V[t], Wt = W[t];
+    const uint32_t meta = lb.meta[t];
+    const int nn = (int)(meta & 0xffu), nlow = (int)((meta >> 8) & 0xffu),
+              ntc = (int)((meta >> 16) & 0xffu);
+    LawConst<double> cpp{p.Es_pp, p.Gs_pp, p.beta, p.mu_s, p.mu_r, p.mu_t, p.dt};
+    V3<double> F = mk(0.0, 0.0, 0.0), T = mk(0.0, 0.0, 0.0);
+    HistD* hpp = static_cast<HistD*>(lb.hpp);
+    for (int k = 0; k < nn; ++k) {
+      const uint32_t u = lb.nbr[(size_t)k * n + t];
+      const D4 Pu = P[u];
+      const bool t_is_i = k >= nlow;  // partner has the higher caller index
+      const D4 Pi = t_is_i ? Pt : Pu, Pj = t_is_i ? Pu : Pt;
+      const V3<double> d = mk(Pi.x - Pj.x, Pi.y - Pj.y, Pi.z - Pj.z);
+      const double d2 = dot(d, d);
+      const double S = Pi.w + Pj.w;
+      if (d2 > S * S * (1.0 + 1e-10)) continue;  // clearly apart
+      const double dist = sqrt(d2);
+      const double delta = S - dist;
+      if (delta < 0.0 || !(dist > 0.0)) continue;
+      const D4 Vu = V[u], Wu = W[u];
+      const D4 Vi = t_is_i ? Vt : Vu, Vj = t_is_i ? Vu : Vt;
+      const D4 Wi = t_is_i ? Wt : Wu, Wj = t_is_i ? Wu : Wt;
+      const V3<double> nh = (1.0 / dist) * d;
+      const double Ri = Pi.w, Rj = Pj.w;
+      const double Rs = 1.0 / (1.0 / Ri + 1.0 / Rj);
+      const double ms = 1.0 / (1.0 / Vi.w + 1.0 / Vj.w);
+      const double ri = Ri - delta / 2.0, rj = Rj - delta / 2.0;
+      HistD h = hpp[(size_t)k * n + t];
+      V3<double> us = mk(0.0, 0.0, 0.0), ur = us;
+      double ut = 0.0;
+      if (h.stamp == stamp_now) {
+        us = mk(h.us[0], h.us[1], h.us[2]);
+        ur = mk(h.ur[0], h.ur[1], h.ur[2]);
+        ut = h.ut;
+      }
+      const LawOut<double> o =
+          contact_law(cpp, nh, delta, Rs, ms, ri, rj, 1.0 / ri + 1.0 / rj, xyz(Vi) - xyz(Vj),
+                      ri * xyz(Wi) + rj * xyz(Wj), xyz(Wi) - xyz(Wj), us, ur, ut);
+      HistD hn;
+      hn.us[0] = us.x; hn.us[1] = us.y; hn.us[2] = us.z;
+      hn.ur[0] = ur.x; hn.ur[1] = ur.y; hn.ur[2] = ur.z;
+      hn.ut = ut;
+      hn.stamp = stamp_new;
+      hn.pad = 0;
+      hpp[(size_t)k * n + t] = hn;
+      if (t_is_i) {
+        F = F + o.f;
+        T = T + o.ti;
+      } else {
+        F = F - o.f;
+        T = T + o.tj;
+      }
+      ++npair;
+    }
+    // particle-triangle contacts
+    if (ntc > 0) {
+      LawConst<double> cpw{p.Es_pw, p.Gs_pw, p.beta, p.mu_s, p.mu_r, p.mu_t, p.dt};
+      HistD* hpm = static_cast<HistD*>(lb.hpm);
+      const V3<double> x = xyz(Pt);
+      const V3<double> Om = mk(p.mesh_omega[0], p.mesh_omega[1], p.mesh_omega[2]);
+      const V3<double> ctr = mk(p.mesh_center[0], p.mesh_center[1], p.mesh_center[2]);
+      for (int m = 0; m < ntc; ++m) {
+        const uint32_t kt = lb.tric[(size_t)m * n + t];
+        const D4 A = mesh.cur[3 * kt], B = mesh.cur[3 * kt + 1], C = mesh.cur[3 * kt + 2];
+        const V3<double> pc = closest_point_triangle(x, xyz(A), xyz(B), xyz(C));
+        const V3<double> d = x - pc;
+        const double dist = sqrt(dot(d, d));
+        const double delta = Pt.w + A.w - dist;
+        if (delta < 0.0 || !(dist > 0.0)) continue;
+        const V3<double> nh = (1.0 / dist) * d;
+        const double ri = Pt.w - delta / 2.0;
+        const V3<double> xc = x - ri * nh;
+        const V3<double> vw = cross(Om, xc - ctr);
+        HistD h = hpm[(size_t)m * n + t];
+        V3<double> us = mk(0.0, 0.0, 0.0), ur = us;
+        double ut = 0.0;
+        if (h.stamp == stamp_now) {
+          us = mk(h.us[0], h.us[1], h.us[2]);
+          ur = mk(h.ur[0], h.ur[1], h.ur[2]);
+          ut = h.ut;
+        }
+        const LawOut<double> o = contact_law(cpw, nh, delta, Pt.w, Vt.w, ri, 0.0, 1.0 / ri,
+                                             xyz(Vt) - vw, ri * xyz(Wt), xyz(Wt) - Om, us, ur, ut);
+        HistD hn;
+        hn.us[0] = us.x; hn.us[1] = us.y; hn.us[2] = us.z;
+        hn.ur[0] = ur.x; hn.ur[1] = ur.y; hn.ur[2] = ur.z;
+        hn.ut = ut;
+        hn.stamp = stamp_new;
+        hn.pad = 0;
+        hpm[(size_t)m * n + t] = hn;
+        F = F + o.f;
+        T = T + o.ti;
+        ++nmesh;
+      }
+    }
+    // semi-implicit Euler + SPIRAL (Sec. 2.3)
+    const double R = Pt.w, mass = Vt.w;
+    const double I = 2.0 / 5.0 * mass * R * R;
+    const double ci = 9.0 * p.eta / (2.0 * p.rho * R * R);
+    const double gi = 10.0 / 3.0 * ci;
+    V3<double> v = xyz(Vt), w = xyz(Wt), x = xyz(Pt);
+    const V3<double> g = mk(p.g[0], p.g[1], p.g[2]);
+    const V3<double> a = (1.0 / mass) * F + g - ci * v;
+    const V3<double> al = (1.0 / I) * T - gi * w;
+    v = v + p.dt * a;
+    x = x + p.dt * v;
+    const D4 q4 = Q[t];
+    double q[4] = {q4.x, q4.y, q4.z, q4.w};
+    const double wn = sqrt(dot(w, w));
+    if (wn > 0.0) {
+      const double phi = p.dt / 2.0 * wn;
+      double sp, cp;
+      sincos(phi, &sp, &cp);
+      const double r[4] = {cp, sp * w.x / wn, sp * w.y / wn, sp * w.z / wn};
+      double o4[4];
+      qmul(q, r, o4);
+      q[0] = o4[0]; q[1] = o4[1]; q[2] = o4[2]; q[3] = o4[3];
+    }
+    const double an = sqrt(dot(al, al));
+    if (an > 0.0) {
+      const double th = (p.dt / 2.0) * (p.dt / 2.0) * an;
+      double st, ct;
+      sincos(th, &st, &ct);
+      const double r[4] = {ct, st * al.x / an, st * al.y / an, st * al.z / an};
+      double o4[4];
+      qmul(q, r, o4);
+      q[0] = o4[0]; q[1] = o4[1]; q[2] = o4[2]; q[3] = o4[3];
+    }
+    w = w + p.dt * al;
+    D4* Pn = static_cast<D4*>(sb.P[ph ^ 1u]);
+    D4* Vn = static_cast<D4*>(sb.V[ph ^ 1u]);
+    D4* Wn = static_cast<D4*>(sb.W[ph ^ 1u]);
+    D4* Qn = static_cast<D4*>(sb.Q[ph ^ 1u]);
+    Pn[t] = make_D4(x.x, x.y, x.z, R);
+    Vn[t] = make_D4(v.x, v.y, v.z, mass);
+    Wn[t] = make_D4(w.x, w.y, w.z, 0.0);
+    Qn[t] = make_D4(q[0], q[1], q[2], q[3]);
+    if (p.record_forces) {
+      double* fo = forces + 6 * (size_t)t;
+      fo[0] = F.x; fo[1] = F.y; fo[2] = F.z;
+      fo[3] = T.x; fo[4] = T.y; fo[5] = T.z;
+    }
+    bad = !isfinite(x.x + x.y + x.z + v.x + v.y + v.z + w.x + w.y + w.z);
+    const float4 pr = lb.posf[t];
+    const float ex = (float)(x.x - p.origin[0]) - pr.x, ey = (float)(x.y - p.origin[1]) - pr.y,
+                ez = (float)(x.z - p.origin[2]) - pr.z;
+    disp = ex * ex + ey * ey + ez * ez >= p.half_skin_trigger * p.half_skin_trigger;
+  }
+  count_and_flag(ctl, npair, nmesh, disp, bad);
+}
+
+}  // namespace
+
+void launch_step_fp64(cudaStream_t st, Ctl* ctl, const Params& p, StateBufs sb, Lists L,
+                      MeshDev mesh, double* forces) {
+  const unsigned nb = (unsigned)((p.n + 127) / 128);
+  k_step_fp64<<<nb, 128, 0, st>>>(ctl, p, sb, L, mesh, forces);
+}
+
+}  // namespace dem

@@ -1,0 +1,259 @@
+"""Thin Python binding of libdem (include/dem.h).
+
+Argument marshalling only: every step of the DEM path runs in the CUDA
+library.  The functions keep the C names; `Scene` is a small convenience
+wrapper that owns a `dem_scene*`.  PyTorch is used only to hand the library
+the current CUDA stream.  If the compiled library is missing this module
+raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdem.so")
+
+DEM_OK = 0
+DEM_ERR_INVALID = 1
+DEM_ERR_CAPACITY = 2
+DEM_ERR_NONFINITE = 3
+DEM_ERR_TIMEOUT = 4
+DEM_ERR_CUDA = 5
+DEM_ERR_NOMEM = 6
+
+DEM_FP64 = 0
+DEM_MIXED = 1
+
+_D = ctypes.c_double
+_I32 = ctypes.c_int32
+_I64 = ctypes.c_int64
+_DP = ctypes.POINTER(ctypes.c_double)
+
+# every symbol declared in include/dem.h
+EXPORTS = ("dem_scene_create", "dem_step", "dem_synchronize", "dem_read_state",
+           "dem_read_forces", "dem_read_contacts", "dem_get_stats", "dem_save", "dem_load",
+           "dem_scene_destroy", "dem_status_string", "dem_step_timed")
+
+
+class dem_params(ctypes.Structure):
+    _fields_ = [("E", _D), ("nu", _D), ("rho", _D), ("e_n", _D), ("mu_s", _D), ("mu_r", _D),
+                ("mu_t", _D), ("eta", _D), ("g", _D * 3), ("dt", _D),
+                ("mesh_omega", _D * 3), ("mesh_center", _D * 3), ("skin", _D),
+                ("domain_lo", _D * 3), ("domain_hi", _D * 3), ("precision", _I32),
+                ("max_neighbors", _I32), ("max_mesh_contacts", _I32),
+                ("record_forces", _I32)]
+
+
+class dem_particles(ctypes.Structure):
+    _fields_ = [("n", _I64), ("R", _DP), ("x", _DP), ("v", _DP), ("w", _DP), ("q", _DP)]
+
+
+class dem_mesh(ctypes.Structure):
+    _fields_ = [("n_vert", _I64), ("vert", _DP), ("n_tri", _I64),
+                ("tri", ctypes.POINTER(ctypes.c_int32)), ("tri_radius", _DP)]
+
+
+class dem_stats(ctypes.Structure):
+    _fields_ = [("steps", _I64), ("rebuilds", _I64), ("pair_contacts", _I64),
+                ("mesh_contacts", _I64), ("list_entries", _I64), ("mesh_candidates", _I64),
+                ("max_list_len", _I32), ("status", _I32), ("launches_per_step", _I32),
+                ("reserved", _I32)]
+
+
+class DemError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {status_string(code)} ({code})")
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libdem.so; raises if it has not been built (no CPU fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libdem.so not built at {path}; run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    lib.dem_scene_create.argtypes = [ctypes.POINTER(dem_params), ctypes.POINTER(dem_particles),
+                                     ctypes.POINTER(dem_mesh), P, ctypes.POINTER(P)]
+    lib.dem_step.argtypes = [P, _I64]
+    lib.dem_synchronize.argtypes = [P]
+    lib.dem_step_timed.argtypes = [P, _I64, _DP]
+    lib.dem_read_state.argtypes = [P, _DP, _DP, _DP, _DP]
+    lib.dem_read_forces.argtypes = [P, _DP, _DP]
+    lib.dem_read_contacts.argtypes = [P, _I64, ctypes.POINTER(_I64), _DP, ctypes.POINTER(_I64)]
+    lib.dem_get_stats.argtypes = [P, ctypes.POINTER(dem_stats)]
+    lib.dem_save.argtypes = [P, P, ctypes.POINTER(ctypes.c_size_t)]
+    lib.dem_load.argtypes = [P, P, ctypes.c_size_t]
+    lib.dem_scene_destroy.argtypes = [P]
+    lib.dem_scene_destroy.restype = None
+    lib.dem_status_string.argtypes = [ctypes.c_int]
+    lib.dem_status_string.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name not in ("dem_scene_destroy", "dem_status_string"):
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def status_string(code: int) -> str:
+    return load().dem_status_string(int(code)).decode()
+
+
+def _check(rc: int, what: str):
+    if rc != DEM_OK:
+        raise DemError(rc, what)
+
+
+def _f64(a, shape):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(shape))
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(_DP)
+
+
+def make_params(p: dict, precision: int = DEM_FP64, skin: float = 0.0, max_neighbors: int = 0,
+                max_mesh_contacts: int = 0, record_forces: bool = False,
+                domain=None) -> dem_params:
+    dp = dem_params()
+    for k in ("E", "nu", "rho", "e_n", "mu_s", "mu_r", "mu_t", "eta", "dt"):
+        setattr(dp, k, float(p[k]))
+    dp.g[:] = [float(c) for c in p.get("g", (0, 0, 0))]
+    dp.mesh_omega[:] = [float(c) for c in p.get("mesh_omega", (0, 0, 0))]
+    dp.mesh_center[:] = [float(c) for c in p.get("mesh_center", (0, 0, 0))]
+    dp.skin = float(skin)
+    if domain is not None:
+        dp.domain_lo[:] = [float(c) for c in domain[0]]
+        dp.domain_hi[:] = [float(c) for c in domain[1]]
+    dp.precision = int(precision)
+    dp.max_neighbors = int(max_neighbors)
+    dp.max_mesh_contacts = int(max_mesh_contacts)
+    dp.record_forces = 1 if record_forces else 0
+    return dp
+
+
+def current_stream():
+    """The current torch CUDA stream as a cudaStream_t (None if torch is absent)."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        pass
+    return None
+
+
+class Scene:
+    """Owner of one `dem_scene*` created from host arrays."""
+
+    def __init__(self, params: dict, R, x, v=None, w=None, q=None, verts=None, tris=None,
+                 tri_radius=None, precision: int = DEM_FP64, skin: float = 0.0,
+                 max_neighbors: int = 0, max_mesh_contacts: int = 0,
+                 record_forces: bool = False, domain=None, stream=None):
+        lib = load()
+        self._lib = lib
+        self._h = ctypes.c_void_p()
+        R = _f64(R, (-1,))
+        n = R.shape[0]
+        self.n = n
+        x = _f64(x, (n, 3))
+        v = None if v is None else _f64(v, (n, 3))
+        w = None if w is None else _f64(w, (n, 3))
+        q = None if q is None else _f64(q, (n, 4))
+        self.precision = precision
+        self._pp = make_params(params, precision, skin, max_neighbors, max_mesh_contacts,
+                               record_forces, domain)
+        pa = dem_particles(n, _p(R), _p(x), _p(v), _p(w), _p(q))
+        keep = [R, x, v, w, q]
+        me = dem_mesh()
+        if tris is not None and len(tris):
+            V = _f64(verts, (-1, 3))
+            T = np.ascontiguousarray(np.asarray(tris, dtype=np.int32).reshape(-1, 3))
+            Rt = None if tri_radius is None else _f64(tri_radius, (-1,))
+            me = dem_mesh(V.shape[0], _p(V), T.shape[0],
+                          T.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _p(Rt))
+            keep += [V, T, Rt]
+        self.n_tri = me.n_tri
+        st = stream if stream is not None else current_stream()
+        rc = lib.dem_scene_create(ctypes.byref(self._pp), ctypes.byref(pa), ctypes.byref(me), st,
+                                  ctypes.byref(self._h))
+        del keep
+        _check(rc, "dem_scene_create")
+
+    @classmethod
+    def from_dict(cls, s: dict, **kw):
+        return cls(s["params"], s["R"], s["x"], s.get("v"), s.get("w"), s.get("q"),
+                   s.get("verts"), s.get("tris"), s.get("tri_radius"), **kw)
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._lib.dem_scene_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, nsteps: int = 1):
+        _check(self._lib.dem_step(self._h, int(nsteps)), "dem_step")
+
+    def step_timed(self, nsteps: int) -> np.ndarray:
+        """Run nsteps phase by phase; device ms of [mesh pose, rebuild, step, advance]."""
+        ms = np.zeros(4)
+        _check(self._lib.dem_step_timed(self._h, int(nsteps), _p(ms)), "dem_step_timed")
+        return ms
+
+    def synchronize(self) -> int:
+        return int(self._lib.dem_synchronize(self._h))
+
+    def state(self) -> dict:
+        n = self.n
+        x, v, w, q = np.empty((n, 3)), np.empty((n, 3)), np.empty((n, 3)), np.empty((n, 4))
+        _check(self._lib.dem_read_state(self._h, _p(x), _p(v), _p(w), _p(q)), "dem_read_state")
+        return {"x": x, "v": v, "w": w, "q": q}
+
+    def read_state_into(self, x, v, w, q) -> int:
+        return int(self._lib.dem_read_state(self._h, _p(x), _p(v), _p(w), _p(q)))
+
+    def forces(self):
+        F, T = np.empty((self.n, 3)), np.empty((self.n, 3))
+        _check(self._lib.dem_read_forces(self._h, _p(F), _p(T)), "dem_read_forces")
+        return F, T
+
+    def contacts(self):
+        cnt = _I64(0)
+        rc = self._lib.dem_read_contacts(self._h, 0, None, None, ctypes.byref(cnt))
+        if rc not in (DEM_OK, DEM_ERR_CAPACITY):
+            _check(rc, "dem_read_contacts")
+        m = cnt.value
+        keys = np.empty((m, 2), dtype=np.int64)
+        hist = np.empty((m, 7))
+        _check(self._lib.dem_read_contacts(self._h, m, keys.ctypes.data_as(ctypes.POINTER(_I64)),
+                                           _p(hist), ctypes.byref(cnt)), "dem_read_contacts")
+        return keys, hist
+
+    def stats(self) -> dict:
+        st = dem_stats()
+        _check(self._lib.dem_get_stats(self._h, ctypes.byref(st)), "dem_get_stats")
+        return {k: getattr(st, k) for k, _ in dem_stats._fields_}
+
+    def save(self) -> bytes:
+        ln = ctypes.c_size_t(0)
+        _check(self._lib.dem_save(self._h, None, ctypes.byref(ln)), "dem_save")
+        buf = ctypes.create_string_buffer(ln.value)
+        _check(self._lib.dem_save(self._h, buf, ctypes.byref(ln)), "dem_save")
+        return buf.raw[:ln.value]
+
+    def load(self, blob: bytes):
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        _check(self._lib.dem_load(self._h, buf, len(blob)), "dem_load")

@@ -158,8 +158,12 @@ def lattice_box_scene(n_side=(10, 10, 10), seed=2, spacing=2.0e-3, r_range=(0.9e
     return _scene("lattice_box", seed, params, R, X, v, w, q, V, T, np.zeros(len(T)), (lo, hi))
 
 
-def column_scene(n=2000, seed=3, median=1.0e-3, sigma=0.2, gap=0.05e-3, **over):
-    """Square column of aspect ratio 2 (height = 2 x width) on a floor mesh."""
+def column_scene(n=2000, seed=3, median=1.0e-3, sigma=0.2, gap=0.05e-3, spacing=None, **over):
+    """Square column of aspect ratio 2 (height = 2 x width) on a floor mesh.
+
+    Particles sit on a jittered cubic lattice of pitch `spacing` (default
+    2 R_max + gap: no overlaps); a smaller pitch gives initial contacts.
+    """
     rng = np.random.default_rng(seed)
     rmin, rmax = median * math.exp(-3 * sigma), median * math.exp(3 * sigma)
     R = np.empty(0)
@@ -167,7 +171,7 @@ def column_scene(n=2000, seed=3, median=1.0e-3, sigma=0.2, gap=0.05e-3, **over):
         s = np.exp(rng.normal(math.log(median), sigma, size=2 * n))
         R = np.concatenate([R, s[(s >= rmin) & (s <= rmax)]])
     R = R[:n]
-    d = 2 * rmax + gap
+    d = 2 * rmax + gap if spacing is None else spacing
     k = 1
     while 2 * k ** 3 < n:
         k += 1
@@ -178,8 +182,8 @@ def column_scene(n=2000, seed=3, median=1.0e-3, sigma=0.2, gap=0.05e-3, **over):
     X = np.empty((n, 3))
     X[:, 0] = (gi[:, 0] - 0.5 * (k - 1)) * d
     X[:, 1] = (gi[:, 1] - 0.5 * (k - 1)) * d
-    X[:, 2] = rmax + gap + gi[:, 2] * d
-    slack = 0.5 * (d - 2 * R)[:, None]
+    X[:, 2] = 0.5 * d + gi[:, 2] * d
+    slack = np.maximum(0.5 * (d - 2 * R), 0.0)[:, None]
     X += rng.uniform(-1.0, 1.0, size=X.shape) * slack * 0.5
     w_col = k * d
     L = 6.0 * w_col
