@@ -168,6 +168,37 @@ int dem_load(dem_scene* s, const void* buf, size_t len);
 
 void dem_scene_destroy(dem_scene* s);
 
+/* Contact force and torque sums of a particle state that has no friction
+ * history yet (the first step of a run), for callers that cannot allocate
+ * device memory: code running inside a CUDA stream capture or a real-time
+ * loop, where an allocation would break the capture or stall, and hosts whose
+ * device memory is owned by another allocator (a framework's caching pool)
+ * that must stay the only one.  The paper has no counterpart of this entry
+ * point; it is a packaging of the library's FP64 first-step arithmetic.
+ *
+ * Inputs and outputs are DEVICE arrays of the caller: R[n], x[n][3], v[n][3],
+ * w[n][3] in, F[n][3] and T[n][3] out (contact sums only: no gravity, no drag).
+ * Only particle pairs are considered (no mesh).  The cell grid covers
+ * params->domain_lo .. domain_hi with cells of edge 2 r_max (r_max >= every R);
+ * particles outside are clamped to the boundary cells.  Material parameters
+ * come from params (precision and list fields are ignored).
+ *
+ * Memory: nothing is allocated.  Scratch is one fixed device array inside the
+ * library (about 3.5 MB, kept by every device that loads the library until
+ * the process exits).  Limits: n <= 131072 particles and at most 262144 grid
+ * cells; larger requests return DEM_ERR_INVALID without launching anything.
+ * More than 64 touching partners of one particle return DEM_ERR_CAPACITY.
+ * The first call on a device looks up the array's device address (set-up, no
+ * allocation); make that first call before any stream capture.  Every call
+ * shares the array and leaves its last contents there; the call clears what
+ * must start at zero.  Calls that overlap on the GPU (other streams, other
+ * threads) race on the array and must be serialised by the caller.  The call
+ * enqueues its kernels on `stream` (a cudaStream_t, NULL = legacy default)
+ * and waits for that stream before returning the status. */
+int dem_contact_forces_noalloc(const dem_params* params, int64_t n, double r_max,
+                               const double* R, const double* x, const double* v,
+                               const double* w, double* F, double* T, void* stream);
+
 const char* dem_status_string(int status);
 
 #ifdef __cplusplus

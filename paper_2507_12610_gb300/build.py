@@ -18,9 +18,10 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdem.so")
 
-SOURCES = ["dem_api.cu", "dem_rebuild.cu", "dem_scan.cu", "dem_step.cu", "dem_step_fp64.cu"]
+SOURCES = ["dem_api.cu", "dem_rebuild.cu", "dem_scan.cu", "dem_step.cu", "dem_step_fp64.cu",
+           "dem_noalloc.cu"]
 # the FP64 step is the precision reference: no multiply-add contraction
-FILE_FLAGS = {"dem_step_fp64.cu": ["--fmad=false"]}
+FILE_FLAGS = {"dem_step_fp64.cu": ["--fmad=false"], "dem_noalloc.cu": ["--fmad=false"]}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -35,7 +35,8 @@ _DP = ctypes.POINTER(ctypes.c_double)
 # every symbol declared in include/dem.h
 EXPORTS = ("dem_scene_create", "dem_step", "dem_synchronize", "dem_read_state",
            "dem_read_forces", "dem_read_contacts", "dem_get_stats", "dem_save", "dem_load",
-           "dem_scene_destroy", "dem_status_string", "dem_step_timed")
+           "dem_scene_destroy", "dem_status_string", "dem_step_timed",
+           "dem_contact_forces_noalloc")
 
 
 class dem_params(ctypes.Structure):
@@ -92,6 +93,8 @@ def load(path: str = LIB_PATH):
     lib.dem_get_stats.argtypes = [P, ctypes.POINTER(dem_stats)]
     lib.dem_save.argtypes = [P, P, ctypes.POINTER(ctypes.c_size_t)]
     lib.dem_load.argtypes = [P, P, ctypes.c_size_t]
+    lib.dem_contact_forces_noalloc.argtypes = [ctypes.POINTER(dem_params), _I64, _D, P, P, P,
+                                               P, P, P, P]
     lib.dem_scene_destroy.argtypes = [P]
     lib.dem_scene_destroy.restype = None
     lib.dem_status_string.argtypes = [ctypes.c_int]
@@ -138,6 +141,21 @@ def make_params(p: dict, precision: int = DEM_FP64, skin: float = 0.0, max_neigh
     dp.max_mesh_contacts = int(max_mesh_contacts)
     dp.record_forces = 1 if record_forces else 0
     return dp
+
+
+def contact_forces_noalloc(params: dict, n: int, r_max: float, R_ptr: int, x_ptr: int,
+                           v_ptr: int, w_ptr: int, F_ptr: int, T_ptr: int, domain,
+                           stream=None) -> int:
+    """dem_contact_forces_noalloc on caller-owned device buffers (raw pointers).
+
+    The library allocates nothing for this call; see include/dem.h for the
+    limits and the set-up made by the first call on a device.
+    """
+    lib = load()
+    dp = make_params(params, domain=domain)
+    st = stream if stream is not None else current_stream()
+    return int(lib.dem_contact_forces_noalloc(ctypes.byref(dp), int(n), float(r_max), R_ptr,
+                                              x_ptr, v_ptr, w_ptr, F_ptr, T_ptr, st))
 
 
 def current_stream():
