@@ -193,19 +193,17 @@ int fetch_contacts(dem_scene* s, const Ctl& c, std::vector<ContactRow>& rows) {
   const int64_t n = s->n;
   const uint32_t lph = c.lphase & 1u;
   const ListBuf& lb = s->L.b[lph];
-  std::vector<uint32_t> gid(n), meta(n);
+  std::vector<uint32_t> gid(n), meta(n), offs(n + 1);
   DEM_TRY(cudaMemcpy(gid.data(), lb.gid, n * 4, cudaMemcpyDeviceToHost));
   DEM_TRY(cudaMemcpy(meta.data(), lb.meta, n * 4, cudaMemcpyDeviceToHost));
-  int maxnn = 0, maxnt = 0;
-  for (int64_t t = 0; t < n; ++t) {
-    maxnn = std::max(maxnn, (int)(meta[t] & 0xffu));
-    maxnt = std::max(maxnt, (int)((meta[t] >> 16) & 0xffu));
-  }
-  std::vector<uint32_t> nbr((size_t)maxnn * n), tric((size_t)maxnt * n);
-  std::vector<unsigned char> hpp((size_t)maxnn * n * s->hist_bytes),
-      hpm((size_t)maxnt * n * s->hist_bytes);
-  if (maxnn) {
-    DEM_TRY(cudaMemcpy(nbr.data(), lb.nbr, nbr.size() * 4, cudaMemcpyDeviceToHost));
+  DEM_TRY(cudaMemcpy(offs.data(), lb.offs, (n + 1) * 4, cudaMemcpyDeviceToHost));
+  int maxnt = 0;
+  for (int64_t t = 0; t < n; ++t) maxnt = std::max(maxnt, (int)((meta[t] >> 16) & 0xffu));
+  const size_t E = offs[n];
+  std::vector<uint32_t> nbr(E), tric((size_t)maxnt * n);
+  std::vector<unsigned char> hpp(E * s->hist_bytes), hpm((size_t)maxnt * n * s->hist_bytes);
+  if (E) {
+    DEM_TRY(cudaMemcpy(nbr.data(), lb.nbr, E * 4, cudaMemcpyDeviceToHost));
     DEM_TRY(cudaMemcpy(hpp.data(), lb.hpp, hpp.size(), cudaMemcpyDeviceToHost));
   }
   if (maxnt) {
@@ -233,11 +231,11 @@ int fetch_contacts(dem_scene* s, const Ctl& c, std::vector<ContactRow>& rows) {
     const int nn = (int)(meta[t] & 0xffu), nt = (int)((meta[t] >> 16) & 0xffu);
     const int64_t i = gid[t];
     for (int k = 0; k < nn; ++k) {
-      const uint32_t u = nbr[(size_t)k * n + t];
+      const uint32_t u = nbr[offs[t] + k];
       const int64_t j = gid[u];
       if (j <= i) continue;
       ContactRow r;
-      decode(&hpp[((size_t)k * n + t) * s->hist_bytes], r);
+      decode(&hpp[((size_t)offs[t] + k) * s->hist_bytes], r);
       if (r.stamp != want || c.step == 0) continue;
       r.i = i;
       r.j = j;
@@ -284,8 +282,12 @@ int install_contacts(dem_scene* s, const std::vector<ContactRow>& rows, uint32_t
     maxnt = std::max(maxnt, pm[i].size());
   }
   if (maxnn > (size_t)s->p.cap || maxnt > (size_t)s->p.capm) return DEM_ERR_CAPACITY;
-  std::vector<uint32_t> meta(n), nbr(maxnn * n), tric(maxnt * n);
-  std::vector<unsigned char> hpp(maxnn * n * s->hist_bytes), hpm(maxnt * n * s->hist_bytes);
+  std::vector<uint32_t> meta(n), offs(n + 1), tric(maxnt * n);
+  offs[0] = 0;
+  for (int64_t i = 0; i < n; ++i) offs[i + 1] = offs[i] + (uint32_t)pp[i].size();
+  const size_t E = offs[n];
+  std::vector<uint32_t> nbr(E);
+  std::vector<unsigned char> hpp(E * s->hist_bytes), hpm(maxnt * n * s->hist_bytes);
   auto encode = [&](const ContactRow& r, unsigned char* rec) {
     if (s->p.mixed) {
       HistM h;
@@ -305,8 +307,8 @@ int install_contacts(dem_scene* s, const std::vector<ContactRow>& rows, uint32_t
   for (int64_t i = 0; i < n; ++i) {
     meta[i] = (uint32_t)pp[i].size() | ((uint32_t)pm[i].size() << 16);
     for (size_t k = 0; k < pp[i].size(); ++k) {
-      nbr[k * n + i] = (uint32_t)pp[i][k].first;
-      encode(*pp[i][k].second, &hpp[(k * n + i) * s->hist_bytes]);
+      nbr[offs[i] + k] = (uint32_t)pp[i][k].first;
+      encode(*pp[i][k].second, &hpp[(offs[i] + k) * s->hist_bytes]);
     }
     for (size_t k = 0; k < pm[i].size(); ++k) {
       tric[k * n + i] = (uint32_t)pm[i][k].first;
@@ -317,7 +319,8 @@ int install_contacts(dem_scene* s, const std::vector<ContactRow>& rows, uint32_t
   for (int64_t i = 0; i < n; ++i) ident[i] = (uint32_t)i;
   DEM_TRY(cudaMemcpy(lb.gid, ident.data(), n * 4, cudaMemcpyHostToDevice));
   DEM_TRY(cudaMemcpy(lb.meta, meta.data(), n * 4, cudaMemcpyHostToDevice));
-  if (maxnn) {
+  DEM_TRY(cudaMemcpy(lb.offs, offs.data(), (n + 1) * 4, cudaMemcpyHostToDevice));
+  if (E) {
     DEM_TRY(cudaMemcpy(lb.nbr, nbr.data(), nbr.size() * 4, cudaMemcpyHostToDevice));
     DEM_TRY(cudaMemcpy(lb.hpp, hpp.data(), hpp.size(), cudaMemcpyHostToDevice));
   }
@@ -380,6 +383,7 @@ int upload_state(dem_scene* s, const double* x, const double* v, const double* w
   for (int b = 0; b < 2; ++b) {
     DEM_TRY(cudaMemcpy(s->L.b[b].gid, ident.data(), n * 4, cudaMemcpyHostToDevice));
     DEM_TRY(cudaMemset(s->L.b[b].meta, 0, n * 4));
+    DEM_TRY(cudaMemset(s->L.b[b].offs, 0, (n + 1) * 4));
   }
   Ctl c{};
   c.step = step;
@@ -464,6 +468,20 @@ int dem_scene_create(const dem_params* params, const dem_particles* parts, const
     p.Es_pw = 1.0 / ((1.0 - nu * nu) / E);
     p.Gs_pw = 1.0 / ((2.0 - nu) / G);
   }
+  p.f_Es_pp = (float)p.Es_pp;
+  p.f_Gs_pp = (float)p.Gs_pp;
+  p.f_Es_pw = (float)p.Es_pw;
+  p.f_Gs_pw = (float)p.Gs_pw;
+  p.f_beta = (float)p.beta;
+  p.f_mu_s = (float)p.mu_s;
+  p.f_mu_r = (float)p.mu_r;
+  p.f_mu_t = (float)p.mu_t;
+  p.f_dt = (float)p.dt;
+  for (int a = 0; a < 3; ++a) {
+    p.f_g[a] = (float)p.g[a];
+    p.f_omega[a] = (float)p.mesh_omega[a];
+  }
+  p.f_drag = (float)(9.0 * p.eta / (2.0 * p.rho));
   p.omega_norm = std::sqrt(p.mesh_omega[0] * p.mesh_omega[0] + p.mesh_omega[1] * p.mesh_omega[1] +
                            p.mesh_omega[2] * p.mesh_omega[2]);
   s->static_mesh = !(p.omega_norm > 0.0);
@@ -601,6 +619,7 @@ int dem_scene_create(const dem_params* params, const dem_particles* parts, const
     lb.gid = M.get<uint32_t>(n);
     lb.posf = M.get<float4>(n);
     lb.meta = M.get<uint32_t>(n);
+    lb.offs = M.get<uint32_t>(n + 1);
     lb.nbr = M.get<uint32_t>((size_t)p.cap * n);
     lb.hpp = M.get<unsigned char>((size_t)p.cap * n * s->hist_bytes);
     if (has_mesh) {
@@ -613,7 +632,10 @@ int dem_scene_create(const dem_params* params, const dem_particles* parts, const
   s->bb.order = M.get<uint32_t>(n);
   s->bb.cell_count = M.get<uint32_t>(ncells);
   s->bb.cell_start = M.get<uint32_t>(ncells + 1);
-  s->bb.block_sums = M.get<uint32_t>(scan_block_sums_size(ncells) + 1);
+  s->bb.block_sums = M.get<uint32_t>(scan_block_sums_size(std::max<int64_t>(ncells, n)) + 1);
+  s->bb.tmp_nbr = M.get<uint32_t>((size_t)p.cap * n);
+  s->bb.tmp_cnt = M.get<uint32_t>(n);
+  s->bb.tmp_offs = M.get<uint32_t>(n + 1);
   if (p.record_forces) s->forces = M.get<double>(6 * (size_t)n);
   if (has_mesh) {
     s->bb.tcell_count = M.get<uint32_t>(ncells);
@@ -670,8 +692,8 @@ int dem_scene_create(const dem_params* params, const dem_particles* parts, const
   }
   // kernels per step: mesh pose, rebuild (prep, clear, count, 3 scan, scatter,
   // cell sort, permute, [mesh: clear, count, 3 scan, check, clear, fill, sort],
-  // list build, end), step, advance
-  s->launches_per_step = (s->static_mesh ? 0 : 1) + 11 + (has_mesh ? 9 : 0) + 2;
+  // list build, 3 scan, compact, end), step, advance
+  s->launches_per_step = (s->static_mesh ? 0 : 1) + 15 + (has_mesh ? 9 : 0) + 2;
   rc = upload_state(s, parts->x, parts->v, parts->w, parts->q, parts->R, 0);
   if (rc != DEM_OK) return fail(rc);
   // pose at step 0 (a static mesh keeps it)
@@ -954,6 +976,7 @@ int dem_load(dem_scene* s, const void* buf, size_t len) {
   for (int b = 0; b < 2; ++b) {
     DEM_TRY(cudaMemcpy(s->L.b[b].gid, ident.data(), n * 4, cudaMemcpyHostToDevice));
     DEM_TRY(cudaMemset(s->L.b[b].meta, 0, n * 4));
+    DEM_TRY(cudaMemset(s->L.b[b].offs, 0, (n + 1) * 4));
   }
   int rc = install_contacts(s, rows, 0, (uint32_t)step);
   if (rc != DEM_OK) return rc;

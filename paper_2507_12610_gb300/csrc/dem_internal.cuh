@@ -61,6 +61,10 @@ struct Params {
   float list_margin;        // conservative float margin of candidate tests
   float rmax;               // largest particle radius
   float mesh_prefilter;     // float margin before the FP64 triangle geometry (mixed)
+  // FP32 copies of the constants for DEM_MIXED (no FP64 conversion in the hot loop)
+  float f_Es_pp, f_Gs_pp, f_Es_pw, f_Gs_pw, f_beta, f_mu_s, f_mu_r, f_mu_t, f_dt;
+  float f_g[3], f_omega[3];
+  float f_drag;             // 9 eta / (2 rho): Stokes rate c = f_drag / R^2
   float center_hi[3], center_lo[3];  // mesh_center - origin as hi/lo floats
   int32_t n;
   int32_t cap;              // pair-list capacity per particle
@@ -115,9 +119,10 @@ struct ListBuf {
   uint32_t* gid;    // [n] caller index of the particle in each slot
   float4* posf;     // [n] shifted position (float) and radius at the rebuild
   uint32_t* meta;   // [n] list length | lower-id count << 8 | triangle count << 16
-  uint32_t* nbr;    // [cap][n] partner slots, ascending partner caller index
+  uint32_t* offs;   // [n + 1] CSR offsets of the pair entries (slot order)
+  uint32_t* nbr;    // [offs[n]] partner slots, ascending partner caller index per particle
+  void* hpp;        // [offs[n]] pair history (HistD or HistM), one record per entry
   uint32_t* tric;   // [capm][n] candidate triangles, ascending
-  void* hpp;        // [cap][n] pair history (HistD or HistM)
   void* hpm;        // [capm][n] triangle history
 };
 
@@ -139,6 +144,9 @@ struct BinBuf {
   uint32_t* cell_start; // [ncells + 1]
   uint32_t* order;      // [n] old slot of each new slot
   uint32_t* block_sums; // scan partials
+  uint32_t* tmp_nbr;    // [cap][n] candidates of the list being built (slot order)
+  uint32_t* tmp_cnt;    // [n] their counts
+  uint32_t* tmp_offs;   // [n + 1] exclusive prefix of the counts
   // triangle cell lists
   uint32_t* tcell_count;  // [ncells]
   uint32_t* tcell_start;  // [ncells + 1]

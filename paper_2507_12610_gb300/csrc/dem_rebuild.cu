@@ -209,11 +209,11 @@ __device__ __forceinline__ void mark_empty(Hist* h) {
 }
 
 // For one new slot t: collect the partners within R_t + R_u + skin (float test
-// with a conservative margin) from the 27 surrounding cells, sort them by
-// caller index, write the list, and carry each pair's friction history over
-// from the particle's previous list (merge of two lists sorted by caller
-// index; a history is kept only if the contact touched in the previous step).
-// Then the same for triangle candidates from the particle's cell.
+// with a conservative margin) from the 27 surrounding cells, sorted by caller
+// index, into the temporary fixed-capacity list, and the triangle candidates
+// of the particle's cell into its triangle list, carrying each triangle
+// contact's history over from the particle's previous list.  The pair list is
+// packed into CSR form by k_list_compact once the counts are scanned.
 template <typename Hist>
 __global__ void __launch_bounds__(128)
 k_list_build(Ctl* ctl, Params p, BinBuf bb, Lists L, MeshDev mesh) {
@@ -250,7 +250,6 @@ k_list_build(Ctl* ctl, Params p, BinBuf bb, Lists L, MeshDev mesh) {
           const float cut = X.w + Y.w + p.skin + p.list_margin;
           if (ddx * ddx + ddy * ddy + ddz * ddz < cut * cut) {
             if (cnt < cap) {
-              // insertion into the sorted candidate array
               const uint32_t g = ln.gid[u];
               int j = cnt;
               while (j > 0 && cand_g[j - 1] > g) {
@@ -270,36 +269,18 @@ k_list_build(Ctl* ctl, Params p, BinBuf bb, Lists L, MeshDev mesh) {
     }
   }
   if (overflow) set_status(ctl, DEM_ERR_CAPACITY);
+  int nlow = 0;
+  for (int k = 0; k < cnt; ++k) {
+    if (cand_g[k] < gt) ++nlow;
+    bb.tmp_nbr[(size_t)k * n + t] = cand_s[k];
+  }
+  bb.tmp_cnt[t] = (uint32_t)cnt;
 
-  // old list of the same particle
+  // triangle candidates (fixed capacity per particle), history carried over
   const uint32_t s = bb.order[t];
   const uint32_t mo = lo.meta[s];
-  const int nn_o = (int)(mo & 0xffu), nt_o = (int)((mo >> 16) & 0xffu);
-  const Hist* hpp_o = static_cast<const Hist*>(lo.hpp);
-  Hist* hpp_n = static_cast<Hist*>(ln.hpp);
+  const int nt_o = (int)((mo >> 16) & 0xffu);
   const uint32_t stamp_now = (uint32_t)ctl->step;  // records written in the previous step
-  int nlow = 0;
-  int ko = 0;
-  uint32_t go = ko < nn_o ? lo.gid[lo.nbr[(size_t)ko * n + s]] : 0xffffffffu;
-  for (int k = 0; k < cnt; ++k) {
-    const uint32_t g = cand_g[k];
-    if (g < gt) ++nlow;
-    ln.nbr[(size_t)k * n + t] = cand_s[k];
-    while (ko < nn_o && go < g) {
-      ++ko;
-      go = ko < nn_o ? lo.gid[lo.nbr[(size_t)ko * n + s]] : 0xffffffffu;
-    }
-    Hist* dst = &hpp_n[(size_t)k * n + t];
-    if (ko < nn_o && go == g) {
-      const Hist h = hpp_o[(size_t)ko * n + s];
-      if (h.stamp == stamp_now) *dst = h;
-      else mark_empty(dst);
-    } else {
-      mark_empty(dst);
-    }
-  }
-
-  // triangle candidates
   int ntc = 0;
   if (mesh.nt > 0) {
     const uint32_t cell = cell_index(p, c);
@@ -339,6 +320,50 @@ k_list_build(Ctl* ctl, Params p, BinBuf bb, Lists L, MeshDev mesh) {
   atomicAdd(&ctl->list_entries, (uint32_t)cnt);
   atomicAdd(&ctl->mesh_candidates, (uint32_t)ntc);
   atomicMax(&ctl->max_list_len, (uint32_t)cnt);
+}
+
+// Pack the new pair lists into CSR form (offsets from the scan of the counts)
+// and carry each pair's friction history over from the particle's previous
+// list: both lists are sorted by partner caller index, so one merge finds the
+// old record; it is kept only if the contact touched in the previous step.
+template <typename Hist>
+__global__ void __launch_bounds__(128)
+k_list_compact(Ctl* ctl, Params p, BinBuf bb, Lists L) {
+  if (!rebuilding(ctl)) return;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = p.n;
+  if (t > n) return;
+  const ListBuf lo = L.b[ctl->lphase & 1u];
+  const ListBuf ln = L.b[(ctl->lphase & 1u) ^ 1u];
+  const uint32_t off = bb.tmp_offs[t];
+  ln.offs[t] = off;
+  if (t == n) return;
+  const int cnt = (int)bb.tmp_cnt[t];
+  const uint32_t s = bb.order[t];
+  const uint32_t off_o = lo.offs[s];
+  const int nn_o = (int)(lo.meta[s] & 0xffu);
+  const Hist* hpp_o = static_cast<const Hist*>(lo.hpp);
+  Hist* hpp_n = static_cast<Hist*>(ln.hpp);
+  const uint32_t stamp_now = (uint32_t)ctl->step;
+  int ko = 0;
+  uint32_t go = ko < nn_o ? lo.gid[lo.nbr[off_o + ko]] : 0xffffffffu;
+  for (int k = 0; k < cnt; ++k) {
+    const uint32_t u = bb.tmp_nbr[(size_t)k * n + t];
+    const uint32_t g = ln.gid[u];
+    ln.nbr[off + k] = u;
+    while (ko < nn_o && go < g) {
+      ++ko;
+      go = ko < nn_o ? lo.gid[lo.nbr[off_o + ko]] : 0xffffffffu;
+    }
+    Hist* dst = &hpp_n[off + k];
+    if (ko < nn_o && go == g) {
+      const Hist h = hpp_o[off_o + ko];
+      if (h.stamp == stamp_now) *dst = h;
+      else mark_empty(dst);
+    } else {
+      mark_empty(dst);
+    }
+  }
 }
 
 __global__ void k_rebuild_prep(Ctl* ctl) {
@@ -386,10 +411,16 @@ void launch_rebuild(cudaStream_t st, Ctl* ctl, const Params& p, StateBufs sb, Li
     k_tri_cell_sort<<<gcells, kThreads, 0, st>>>(ctl, p, bb);
   }
   const unsigned nb128 = blocks_for(p.n, 128);
+  const unsigned nb128p = blocks_for((int64_t)p.n + 1, 128);
   if (p.mixed)
     k_list_build<HistM><<<nb128, 128, 0, st>>>(ctl, p, bb, L, mesh);
   else
     k_list_build<HistD><<<nb128, 128, 0, st>>>(ctl, p, bb, L, mesh);
+  launch_scan(st, ctl, bb.tmp_cnt, bb.tmp_offs, p.n, bb.block_sums);
+  if (p.mixed)
+    k_list_compact<HistM><<<nb128p, 128, 0, st>>>(ctl, p, bb, L);
+  else
+    k_list_compact<HistD><<<nb128p, 128, 0, st>>>(ctl, p, bb, L);
   k_rebuild_end<<<1, 1, 0, st>>>(ctl, p);
 }
 

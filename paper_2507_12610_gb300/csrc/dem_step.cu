@@ -18,6 +18,7 @@
 #include "dem_law.cuh"
 #include "dem_math.cuh"
 #include "dem_step_common.cuh"
+#include "dem_step_warp.cuh"
 
 namespace dem {
 
@@ -99,113 +100,139 @@ __device__ __forceinline__ void acc(float& hi, float& lo, float b) {
   lo = s.lo;
 }
 
-__global__ void __launch_bounds__(128)
-k_step_mixed(Ctl* ctl, Params p, StateBufs sb, Lists L, MeshDev mesh, double* forces) {
-  if (ctl->status) return;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  const int n = p.n;
-  const uint32_t ph = ctl->phase & 1u, lph = ctl->lphase & 1u;
-  const uint32_t stamp_now = (uint32_t)ctl->step;
-  const uint32_t stamp_new = stamp_now + 1u;
-  uint32_t npair = 0, nmesh = 0;
-  bool disp = false, bad = false;
-  if (t < n) {
+struct MixedPolicy {
+  static constexpr int kMinBlocks = 5;  // resident blocks per SM the registers must allow
+  using Rec = F8;
+  using Hist = HistM;
+  using T = float;
+
+  struct Acc {
+    Acc3 F, T;
+    __device__ __forceinline__ void zero() {
+      F.zero();
+      T.zero();
+    }
+    __device__ __forceinline__ void add(const float* c) {
+      F.add(mk(c[0], c[1], c[2]));
+      T.add(mk(c[3], c[4], c[5]));
+    }
+  };
+
+  struct Geo {
+    float delta, dist;
+    V3<float> n;
+  };
+
+  // Overlap of the canonical pair (i, j).  The hi words of the shifted
+  // positions share a binade, so their difference is exact; the lo words add
+  // the remaining bits.  delta = (S^2 - d^2) / (S + d) in compensated FP32.
+  static __device__ __forceinline__ bool touch(const Params&, const F8& Pi, const F8& Pj,
+                                               Geo& g) {
+    const float dxh = Pi.hi.x - Pj.hi.x, dyh = Pi.hi.y - Pj.hi.y, dzh = Pi.hi.z - Pj.hi.z;
+    const float dxl = Pi.lo.x - Pj.lo.x, dyl = Pi.lo.y - Pj.lo.y, dzl = Pi.lo.z - Pj.lo.z;
+    const V3<float> dq = mk(dxh + dxl, dyh + dyl, dzh + dzl);
+    const float Sf = (Pi.hi.w + Pi.lo.w) + (Pj.hi.w + Pj.lo.w);
+    if (dot(dq, dq) > Sf * Sf * 1.0001f) return false;  // clearly apart
+    ff sx = two_prod(dxh, dxh);
+    sx.lo = __fmaf_rn(2.f * dxh, dxl, sx.lo);
+    ff sy = two_prod(dyh, dyh);
+    sy.lo = __fmaf_rn(2.f * dyh, dyl, sy.lo);
+    ff sz = two_prod(dzh, dzh);
+    sz.lo = __fmaf_rn(2.f * dzh, dzl, sz.lo);
+    const ff d2 = ff_add(ff_add(sx, sy), sz);
+    ff S = two_sum(Pi.hi.w, Pj.hi.w);
+    S.lo += Pi.lo.w + Pj.lo.w;
+    S = fast_two_sum(S.hi, S.lo);
+    ff S2 = two_prod(S.hi, S.hi);
+    S2.lo = __fmaf_rn(2.f * S.hi, S.lo, S2.lo);
+    const ff df = ff_add(S2, ff_neg(d2));
+    const float num = df.hi + df.lo;
+    if (num < 0.f) return false;
+    const float dist = sqrtf(d2.hi + d2.lo);
+    if (!(dist > 0.f)) return false;
+    g.dist = dist;
+    g.delta = num / ((S.hi + S.lo) + dist);
+    g.n = (1.f / dist) * dq;
+    return true;
+  }
+
+  // Conservative overlap pre-test (symmetric in its arguments): FP32 centre
+  // distance against (R_i + R_j) with a 1e-4 relative margin, far above its
+  // rounding error.
+  static __device__ __forceinline__ bool near(const F8& a, const F8& b) {
+    const V3<float> dq = diff3(a, b);
+    const float Sf = (a.hi.w + a.lo.w) + (b.hi.w + b.lo.w);
+    return dot(dq, dq) <= Sf * Sf * 1.0001f;
+  }
+
+  // Contact law of a canonical pair: if it touches, updates the history and
+  // writes the force/torque on the lane's own particle (i if t_is_i, else j)
+  // to c6 and returns true.
+  static __device__ __forceinline__ bool pair(const Params& p, bool t_is_i, const F8& Pi,
+                                              const F8& Pj, const F8& Vi, const F8& Vj,
+                                              const F8& Wi, const F8& Wj, HistM& h,
+                                              uint32_t stamp_now, uint32_t stamp_new,
+                                              float c6[6]) {
+    Geo g;
+    if (!touch(p, Pi, Pj, g)) return false;
+    const LawConst<float> cpp{p.f_Es_pp, p.f_Gs_pp, p.f_beta, p.f_mu_s, p.f_mu_r, p.f_mu_t,
+                              p.f_dt};
+    const float Ri = Pi.hi.w + Pi.lo.w, Rj = Pj.hi.w + Pj.lo.w;
+    const float Rs = 1.f / (1.f / Ri + 1.f / Rj);
+    const float ms = 1.f / (1.f / Vi.hi.w + 1.f / Vj.hi.w);
+    const float ri = Ri - 0.5f * g.delta, rj = Rj - 0.5f * g.delta;
+    V3<float> us = mk(0.f, 0.f, 0.f), ur = us;
+    float ut = 0.f;
+    if (h.stamp == stamp_now) {
+      us = mk(h.us[0], h.us[1], h.us[2]);
+      ur = mk(h.ur[0], h.ur[1], h.ur[2]);
+      ut = h.ut;
+    }
+    const LawOut<float> o =
+        contact_law(cpp, g.n, g.delta, Rs, ms, ri, rj, 1.f / ri + 1.f / rj, diff3(Vi, Vj),
+                    ri * sum3(Wi) + rj * sum3(Wj), diff3(Wi, Wj), us, ur, ut);
+    h.us[0] = us.x; h.us[1] = us.y; h.us[2] = us.z;
+    h.ur[0] = ur.x; h.ur[1] = ur.y; h.ur[2] = ur.z;
+    h.ut = ut;
+    h.stamp = stamp_new;
+    if (t_is_i) {
+      c6[0] = o.f.x; c6[1] = o.f.y; c6[2] = o.f.z;
+      c6[3] = o.ti.x; c6[4] = o.ti.y; c6[5] = o.ti.z;
+    } else {
+      c6[0] = -o.f.x; c6[1] = -o.f.y; c6[2] = -o.f.z;
+      c6[3] = o.tj.x; c6[4] = o.tj.y; c6[5] = o.tj.z;
+    }
+    return true;
+  }
+
+  // Triangle contacts and integration of particle slot t.
+  static __device__ __forceinline__ void finish(const Params& p, const StateBufs& sb,
+                                                uint32_t ph, const ListBuf& lb,
+                                                const MeshDev& mesh, int t, uint32_t ntc_u,
+                                                Acc& sums, uint32_t stamp_now, uint32_t stamp_new,
+                                                double* forces, uint32_t& nmesh, bool& disp,
+                                                bool& bad) {
+    const int n = p.n;
+    const int ntc = (int)ntc_u;
     const F8* P = static_cast<const F8*>(sb.P[ph]);
     const F8* V = static_cast<const F8*>(sb.V[ph]);
     const F8* W = static_cast<const F8*>(sb.W[ph]);
     const F8* Q = static_cast<const F8*>(sb.Q[ph]);
-    const ListBuf lb = L.b[lph];
     const F8 Pt = P[t], Vt = V[t], Wt = W[t];
-    const uint32_t meta = lb.meta[t];
-    const int nn = (int)(meta & 0xffu), nlow = (int)((meta >> 8) & 0xffu),
-              ntc = (int)((meta >> 16) & 0xffu);
-    const LawConst<float> cpp{(float)p.Es_pp, (float)p.Gs_pp, (float)p.beta, (float)p.mu_s,
-                              (float)p.mu_r, (float)p.mu_t, (float)p.dt};
-    Acc3 F, T;
-    F.zero();
-    T.zero();
-    HistM* hpp = static_cast<HistM*>(lb.hpp);
     const float Rt = Pt.hi.w + Pt.lo.w;
-    for (int k = 0; k < nn; ++k) {
-      const uint32_t u = lb.nbr[(size_t)k * n + t];
-      const F8 Pu = P[u];
-      const bool t_is_i = k >= nlow;
-      const F8 Pi = t_is_i ? Pt : Pu, Pj = t_is_i ? Pu : Pt;
-      // centre distance: hi parts share a binade (shifted coordinates), so
-      // their difference is exact; the lo parts add the remaining bits
-      const float dxh = Pi.hi.x - Pj.hi.x, dyh = Pi.hi.y - Pj.hi.y, dzh = Pi.hi.z - Pj.hi.z;
-      const float dxl = Pi.lo.x - Pj.lo.x, dyl = Pi.lo.y - Pj.lo.y, dzl = Pi.lo.z - Pj.lo.z;
-      const V3<float> dq = mk(dxh + dxl, dyh + dyl, dzh + dzl);
-      const float Sf = (Pi.hi.w + Pi.lo.w) + (Pj.hi.w + Pj.lo.w);
-      const float d2f = dot(dq, dq);
-      if (d2f > Sf * Sf * 1.0001f) continue;  // clearly apart
-      // overlap delta = (S^2 - d^2) / (S + d) in compensated arithmetic
-      ff sx = two_prod(dxh, dxh);
-      sx.lo = __fmaf_rn(2.f * dxh, dxl, sx.lo);
-      ff sy = two_prod(dyh, dyh);
-      sy.lo = __fmaf_rn(2.f * dyh, dyl, sy.lo);
-      ff sz = two_prod(dzh, dzh);
-      sz.lo = __fmaf_rn(2.f * dzh, dzl, sz.lo);
-      const ff d2 = ff_add(ff_add(sx, sy), sz);
-      ff S = two_sum(Pi.hi.w, Pj.hi.w);
-      S.lo += Pi.lo.w + Pj.lo.w;
-      S = fast_two_sum(S.hi, S.lo);
-      ff S2 = two_prod(S.hi, S.hi);
-      S2.lo = __fmaf_rn(2.f * S.hi, S.lo, S2.lo);
-      const ff df = ff_add(S2, ff_neg(d2));
-      const float num = df.hi + df.lo;
-      if (num < 0.f) continue;
-      const float dist = sqrtf(d2.hi + d2.lo);
-      if (!(dist > 0.f)) continue;
-      const float delta = num / ((S.hi + S.lo) + dist);
-      const F8 Vu = V[u], Wu = W[u];
-      const F8 Vi = t_is_i ? Vt : Vu, Vj = t_is_i ? Vu : Vt;
-      const F8 Wi = t_is_i ? Wt : Wu, Wj = t_is_i ? Wu : Wt;
-      const float idist = 1.f / dist;
-      const V3<float> nh = idist * dq;
-      const float Ri = Pi.hi.w + Pi.lo.w, Rj = Pj.hi.w + Pj.lo.w;
-      const float Rs = 1.f / (1.f / Ri + 1.f / Rj);
-      const float ms = 1.f / (1.f / Vi.hi.w + 1.f / Vj.hi.w);
-      const float ri = Ri - 0.5f * delta, rj = Rj - 0.5f * delta;
-      HistM* hp = &hpp[(size_t)k * n + t];
-      const HistM h = *hp;
-      V3<float> us = mk(0.f, 0.f, 0.f), ur = us;
-      float ut = 0.f;
-      if (h.stamp == stamp_now) {
-        us = mk(h.us[0], h.us[1], h.us[2]);
-        ur = mk(h.ur[0], h.ur[1], h.ur[2]);
-        ut = h.ut;
-      }
-      const LawOut<float> o =
-          contact_law(cpp, nh, delta, Rs, ms, ri, rj, 1.f / ri + 1.f / rj, diff3(Vi, Vj),
-                      ri * sum3(Wi) + rj * sum3(Wj), diff3(Wi, Wj), us, ur, ut);
-      HistM hn;
-      hn.us[0] = us.x; hn.us[1] = us.y; hn.us[2] = us.z;
-      hn.ur[0] = ur.x; hn.ur[1] = ur.y; hn.ur[2] = ur.z;
-      hn.ut = ut;
-      hn.stamp = stamp_new;
-      *hp = hn;
-      if (t_is_i) {
-        F.add(o.f);
-        T.add(o.ti);
-      } else {
-        F.add(-o.f);
-        T.add(o.tj);
-      }
-      ++npair;
-    }
+    Acc3& F = sums.F;
+    Acc3& T = sums.T;
     // particle-triangle contacts: float pre-filter, then the geometry of the
     // near candidates in FP64 (a triangle is large compared with the overlap)
     if (ntc > 0) {
-      const LawConst<float> cpw{(float)p.Es_pw, (float)p.Gs_pw, (float)p.beta, (float)p.mu_s,
-                                (float)p.mu_r, (float)p.mu_t, (float)p.dt};
+      const LawConst<float> cpw{p.f_Es_pw, p.f_Gs_pw, p.f_beta, p.f_mu_s, p.f_mu_r, p.f_mu_t,
+                                p.f_dt};
       HistM* hpm = static_cast<HistM*>(lb.hpm);
       const V3<float> qf = sum3(Pt);
       const V3<double> xd = mk(p.origin[0] + ((double)Pt.hi.x + (double)Pt.lo.x),
                                p.origin[1] + ((double)Pt.hi.y + (double)Pt.lo.y),
                                p.origin[2] + ((double)Pt.hi.z + (double)Pt.lo.z));
-      const V3<float> Om = mk((float)p.mesh_omega[0], (float)p.mesh_omega[1],
-                              (float)p.mesh_omega[2]);
+      const V3<float> Om = mk(p.f_omega[0], p.f_omega[1], p.f_omega[2]);
       // particle centre relative to the rotation axis point, accurately
       const V3<float> rc = mk((Pt.hi.x - p.center_hi[0]) + (Pt.lo.x - p.center_lo[0]),
                               (Pt.hi.y - p.center_hi[1]) + (Pt.lo.y - p.center_lo[1]),
@@ -259,14 +286,14 @@ k_step_mixed(Ctl* ctl, Params p, StateBufs sb, Lists L, MeshDev mesh, double* fo
     const float mass = Vt.hi.w;
     const float R = Rt;
     const float I = 0.4f * mass * R * R;
-    const float ci = (float)(9.0 * p.eta / (2.0 * p.rho)) / (R * R);
+    const float ci = p.f_drag / (R * R);
     const float gi = 10.f / 3.f * ci;
-    const float dt = (float)p.dt;
+    const float dt = p.f_dt;
     const V3<float> v0 = sum3(Vt), w0 = sum3(Wt);
     const float im = 1.f / mass, iI = 1.f / I;
-    const V3<float> a = mk((F.hx + F.lx) * im + (float)p.g[0] - ci * v0.x,
-                           (F.hy + F.ly) * im + (float)p.g[1] - ci * v0.y,
-                           (F.hz + F.lz) * im + (float)p.g[2] - ci * v0.z);
+    const V3<float> a = mk((F.hx + F.lx) * im + p.f_g[0] - ci * v0.x,
+                           (F.hy + F.ly) * im + p.f_g[1] - ci * v0.y,
+                           (F.hz + F.lz) * im + p.f_g[2] - ci * v0.z);
     const V3<float> al = mk((T.hx + T.lx) * iI - gi * w0.x, (T.hy + T.ly) * iI - gi * w0.y,
                             (T.hz + T.lz) * iI - gi * w0.z);
     F8 Vn = Vt, Pn = Pt, Wn = Wt, Qn = Q[t];
@@ -331,9 +358,8 @@ k_step_mixed(Ctl* ctl, Params p, StateBufs sb, Lists L, MeshDev mesh, double* fo
     const float ex = (Pn.hi.x - pr.x) + Pn.lo.x, ey = (Pn.hi.y - pr.y) + Pn.lo.y,
                 ez = (Pn.hi.z - pr.z) + Pn.lo.z;
     disp = ex * ex + ey * ey + ez * ez >= p.half_skin_trigger * p.half_skin_trigger;
-  }
-  count_and_flag(ctl, npair, nmesh, disp, bad);
-}
+    }
+};
 
 }  // namespace
 
@@ -344,9 +370,9 @@ void launch_mesh_pose(cudaStream_t st, const Ctl* ctl, const Params& p, MeshDev 
 
 void launch_step(cudaStream_t st, Ctl* ctl, const Params& p, StateBufs sb, Lists L,
                  MeshDev mesh, double* forces) {
-  const unsigned nb = (unsigned)((p.n + 127) / 128);
   if (p.mixed)
-    k_step_mixed<<<nb, 128, 0, st>>>(ctl, p, sb, L, mesh, forces);
+    k_step_warp<MixedPolicy><<<(unsigned)((p.n + kStepThreads - 1) / kStepThreads), kStepThreads,
+                               0, st>>>(ctl, p, sb, L, mesh, forces);
   else
     launch_step_fp64(st, ctl, p, sb, L, mesh, forces);
 }

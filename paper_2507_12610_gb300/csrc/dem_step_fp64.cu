@@ -10,6 +10,7 @@
 #include "dem_law.cuh"
 #include "dem_math.cuh"
 #include "dem_step_common.cuh"
+#include "dem_step_warp.cuh"
 
 namespace dem {
 
@@ -19,76 +20,103 @@ namespace {
 // DEM_FP64
 // ============================================================================
 
-__global__ void __launch_bounds__(128)
-k_step_fp64(Ctl* ctl, Params p, StateBufs sb, Lists L, MeshDev mesh, double* forces) {
-  if (ctl->status) return;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  const int n = p.n;
-  const uint32_t ph = ctl->phase & 1u, lph = ctl->lphase & 1u;
-  const uint32_t stamp_now = (uint32_t)ctl->step;
-  const uint32_t stamp_new = stamp_now + 1u;
-  uint32_t npair = 0, nmesh = 0;
-  bool disp = false, bad = false;
-  if (t < n) {
+struct Fp64Policy {
+  static constexpr int kMinBlocks = 4;  // resident blocks per SM the registers must allow
+  using Rec = D4;
+  using Hist = HistD;
+  using T = double;
+
+  struct Acc {
+    V3<double> F, T;
+    __device__ __forceinline__ void zero() {
+      F = mk(0.0, 0.0, 0.0);
+      T = F;
+    }
+    __device__ __forceinline__ void add(const double* c) {
+      F = F + mk(c[0], c[1], c[2]);
+      T = T + mk(c[3], c[4], c[5]);
+    }
+  };
+
+  struct Geo {
+    double delta, dist;
+    V3<double> d;
+  };
+
+  // Overlap of the canonical pair (i, j), as the paper writes it:
+  // d = x_i - x_j, delta = R_i + R_j - |d|.
+  static __device__ __forceinline__ bool touch(const Params&, const D4& Pi, const D4& Pj,
+                                               Geo& g) {
+    g.d = mk(Pi.x - Pj.x, Pi.y - Pj.y, Pi.z - Pj.z);
+    const double d2 = dot(g.d, g.d);
+    const double S = Pi.w + Pj.w;
+    if (d2 > S * S * (1.0 + 1e-10)) return false;  // clearly apart
+    g.dist = sqrt(d2);
+    g.delta = S - g.dist;
+    return g.delta >= 0.0 && g.dist > 0.0;
+  }
+
+  // Conservative overlap pre-test, symmetric in its arguments (the exact test
+  // is touch() in canonical orientation).
+  static __device__ __forceinline__ bool near(const D4& a, const D4& b) {
+    const V3<double> d = mk(a.x - b.x, a.y - b.y, a.z - b.z);
+    const double S = a.w + b.w;
+    return dot(d, d) <= S * S * (1.0 + 1e-10);
+  }
+
+  static __device__ __forceinline__ bool pair(const Params& p, bool t_is_i, const D4& Pi,
+                                              const D4& Pj, const D4& Vi, const D4& Vj,
+                                              const D4& Wi, const D4& Wj, HistD& h,
+                                              uint32_t stamp_now, uint32_t stamp_new,
+                                              double c6[6]) {
+    Geo g;
+    if (!touch(p, Pi, Pj, g)) return false;
+    const LawConst<double> cpp{p.Es_pp, p.Gs_pp, p.beta, p.mu_s, p.mu_r, p.mu_t, p.dt};
+    const V3<double> nh = (1.0 / g.dist) * g.d;
+    const double Ri = Pi.w, Rj = Pj.w;
+    const double Rs = 1.0 / (1.0 / Ri + 1.0 / Rj);
+    const double ms = 1.0 / (1.0 / Vi.w + 1.0 / Vj.w);
+    const double ri = Ri - g.delta / 2.0, rj = Rj - g.delta / 2.0;
+    V3<double> us = mk(0.0, 0.0, 0.0), ur = us;
+    double ut = 0.0;
+    if (h.stamp == stamp_now) {
+      us = mk(h.us[0], h.us[1], h.us[2]);
+      ur = mk(h.ur[0], h.ur[1], h.ur[2]);
+      ut = h.ut;
+    }
+    const LawOut<double> o =
+        contact_law(cpp, nh, g.delta, Rs, ms, ri, rj, 1.0 / ri + 1.0 / rj, xyz(Vi) - xyz(Vj),
+                    ri * xyz(Wi) + rj * xyz(Wj), xyz(Wi) - xyz(Wj), us, ur, ut);
+    h.us[0] = us.x; h.us[1] = us.y; h.us[2] = us.z;
+    h.ur[0] = ur.x; h.ur[1] = ur.y; h.ur[2] = ur.z;
+    h.ut = ut;
+    h.stamp = stamp_new;
+    h.pad = 0;
+    if (t_is_i) {
+      c6[0] = o.f.x; c6[1] = o.f.y; c6[2] = o.f.z;
+      c6[3] = o.ti.x; c6[4] = o.ti.y; c6[5] = o.ti.z;
+    } else {
+      c6[0] = -o.f.x; c6[1] = -o.f.y; c6[2] = -o.f.z;
+      c6[3] = o.tj.x; c6[4] = o.tj.y; c6[5] = o.tj.z;
+    }
+    return true;
+  }
+
+  static __device__ __forceinline__ void finish(const Params& p, const StateBufs& sb,
+                                                uint32_t ph, const ListBuf& lb,
+                                                const MeshDev& mesh, int t, uint32_t ntc_u,
+                                                Acc& sums, uint32_t stamp_now,
+                                                uint32_t stamp_new, double* forces,
+                                                uint32_t& nmesh, bool& disp, bool& bad) {
+    const int n = p.n;
+    const int ntc = (int)ntc_u;
     const D4* P = static_cast<const D4*>(sb.P[ph]);
     const D4* V = static_cast<const D4*>(sb.V[ph]);
     const D4* W = static_cast<const D4*>(sb.W[ph]);
     const D4* Q = static_cast<const D4*>(sb.Q[ph]);
-    const ListBuf lb = L.b[lph];
     const D4 Pt = P[t], Vt = V[t], Wt = W[t];
-    const uint32_t meta = lb.meta[t];
-    const int nn = (int)(meta & 0xffu), nlow = (int)((meta >> 8) & 0xffu),
-              ntc = (int)((meta >> 16) & 0xffu);
-    LawConst<double> cpp{p.Es_pp, p.Gs_pp, p.beta, p.mu_s, p.mu_r, p.mu_t, p.dt};
-    V3<double> F = mk(0.0, 0.0, 0.0), T = mk(0.0, 0.0, 0.0);
-    HistD* hpp = static_cast<HistD*>(lb.hpp);
-    for (int k = 0; k < nn; ++k) {
-      const uint32_t u = lb.nbr[(size_t)k * n + t];
-      const D4 Pu = P[u];
-      const bool t_is_i = k >= nlow;  // partner has the higher caller index
-      const D4 Pi = t_is_i ? Pt : Pu, Pj = t_is_i ? Pu : Pt;
-      const V3<double> d = mk(Pi.x - Pj.x, Pi.y - Pj.y, Pi.z - Pj.z);
-      const double d2 = dot(d, d);
-      const double S = Pi.w + Pj.w;
-      if (d2 > S * S * (1.0 + 1e-10)) continue;  // clearly apart
-      const double dist = sqrt(d2);
-      const double delta = S - dist;
-      if (delta < 0.0 || !(dist > 0.0)) continue;
-      const D4 Vu = V[u], Wu = W[u];
-      const D4 Vi = t_is_i ? Vt : Vu, Vj = t_is_i ? Vu : Vt;
-      const D4 Wi = t_is_i ? Wt : Wu, Wj = t_is_i ? Wu : Wt;
-      const V3<double> nh = (1.0 / dist) * d;
-      const double Ri = Pi.w, Rj = Pj.w;
-      const double Rs = 1.0 / (1.0 / Ri + 1.0 / Rj);
-      const double ms = 1.0 / (1.0 / Vi.w + 1.0 / Vj.w);
-      const double ri = Ri - delta / 2.0, rj = Rj - delta / 2.0;
-      HistD h = hpp[(size_t)k * n + t];
-      V3<double> us = mk(0.0, 0.0, 0.0), ur = us;
-      double ut = 0.0;
-      if (h.stamp == stamp_now) {
-        us = mk(h.us[0], h.us[1], h.us[2]);
-        ur = mk(h.ur[0], h.ur[1], h.ur[2]);
-        ut = h.ut;
-      }
-      const LawOut<double> o =
-          contact_law(cpp, nh, delta, Rs, ms, ri, rj, 1.0 / ri + 1.0 / rj, xyz(Vi) - xyz(Vj),
-                      ri * xyz(Wi) + rj * xyz(Wj), xyz(Wi) - xyz(Wj), us, ur, ut);
-      HistD hn;
-      hn.us[0] = us.x; hn.us[1] = us.y; hn.us[2] = us.z;
-      hn.ur[0] = ur.x; hn.ur[1] = ur.y; hn.ur[2] = ur.z;
-      hn.ut = ut;
-      hn.stamp = stamp_new;
-      hn.pad = 0;
-      hpp[(size_t)k * n + t] = hn;
-      if (t_is_i) {
-        F = F + o.f;
-        T = T + o.ti;
-      } else {
-        F = F - o.f;
-        T = T + o.tj;
-      }
-      ++npair;
-    }
+    V3<double>& F = sums.F;
+    V3<double>& T = sums.T;
     // particle-triangle contacts
     if (ntc > 0) {
       LawConst<double> cpw{p.Es_pw, p.Gs_pw, p.beta, p.mu_s, p.mu_r, p.mu_t, p.dt};
@@ -182,16 +210,15 @@ k_step_fp64(Ctl* ctl, Params p, StateBufs sb, Lists L, MeshDev mesh, double* for
     const float ex = (float)(x.x - p.origin[0]) - pr.x, ey = (float)(x.y - p.origin[1]) - pr.y,
                 ez = (float)(x.z - p.origin[2]) - pr.z;
     disp = ex * ex + ey * ey + ez * ez >= p.half_skin_trigger * p.half_skin_trigger;
-  }
-  count_and_flag(ctl, npair, nmesh, disp, bad);
-}
+    }
+};
 
 }  // namespace
 
 void launch_step_fp64(cudaStream_t st, Ctl* ctl, const Params& p, StateBufs sb, Lists L,
                       MeshDev mesh, double* forces) {
-  const unsigned nb = (unsigned)((p.n + 127) / 128);
-  k_step_fp64<<<nb, 128, 0, st>>>(ctl, p, sb, L, mesh, forces);
+  k_step_warp<Fp64Policy><<<(unsigned)((p.n + kStepThreads - 1) / kStepThreads), kStepThreads, 0,
+                            st>>>(ctl, p, sb, L, mesh, forces);
 }
 
 }  // namespace dem

@@ -1,0 +1,170 @@
+// Warp-cooperative step kernel shared by both precisions.
+//
+// A warp owns 32 consecutive particle slots.  Their list entries are
+// contiguous in the CSR list, so:
+//   A. the lanes walk the warp's flattened entries 32 at a time (coalesced
+//      list reads), pre-test each pair for overlap with a cheap conservative
+//      test, and append the candidates to a per-warp queue in shared memory;
+//      the queue is in entry order, so each particle's contacts are contiguous
+//      and in ascending partner index;
+//   B. the lanes evaluate the contact law for 32 queued contacts at a time
+//      (all lanes busy), write the friction history, and park each contact's
+//      force/torque on its own particle in shared memory; then every lane adds
+//      the parked contributions of its own particle in queue order;
+//   C. each lane finishes its particle: triangle contacts, integration.
+// The sum of every particle is therefore taken in exactly the order of the
+// per-particle loop (ascending partner caller index, then triangle index),
+// whatever the launch shape.  Policies supply the precision-specific parts.
+#pragma once
+
+#include "dem_internal.cuh"
+#include "dem_math.cuh"
+#include "dem_step_common.cuh"
+
+namespace dem {
+
+constexpr int kStepWarps = 4;             // warps per block
+constexpr int kStepThreads = 32 * kStepWarps;
+constexpr int kQueueMax = 32 * 64;        // a particle has at most 64 list entries
+
+template <typename CT>
+struct WarpScratch {
+  uint32_t seg[33];     // entry prefix of the warp's particles
+  uint32_t istart[33];  // queued-contact prefix of the warp's particles
+  uint32_t cnt[32];
+  uint8_t nlow[32];
+  uint16_t queue[kQueueMax];  // (particle << 6) | entry
+  CT contrib[32][6];
+};
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += t;
+  }
+  return v;
+}
+
+template <typename Pol>
+__global__ void __launch_bounds__(kStepThreads, Pol::kMinBlocks)
+k_step_warp(Ctl* ctl, Params p, StateBufs sb, Lists L, MeshDev mesh, double* forces) {
+  using Rec = typename Pol::Rec;
+  using Hist = typename Pol::Hist;
+  using CT = typename Pol::T;
+  __shared__ WarpScratch<CT> smem[kStepWarps];
+  if (ctl->status) return;
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  WarpScratch<CT>& S = smem[wib];
+  const int n = p.n;
+  const int w0 = (blockIdx.x * kStepWarps + wib) * 32;
+  const int t = w0 + lane;
+  const bool valid = t < n;
+  const uint32_t ph = ctl->phase & 1u, lph = ctl->lphase & 1u;
+  const uint32_t stamp_now = (uint32_t)ctl->step;
+  const uint32_t stamp_new = stamp_now + 1u;
+  const Rec* P = static_cast<const Rec*>(sb.P[ph]);
+  const Rec* V = static_cast<const Rec*>(sb.V[ph]);
+  const Rec* W = static_cast<const Rec*>(sb.W[ph]);
+  const ListBuf lb = L.b[lph];
+  Hist* H = static_cast<Hist*>(lb.hpp);
+
+  const uint32_t meta = valid ? lb.meta[t] : 0u;
+  const uint32_t nn = meta & 0xffu;
+  const uint32_t incl = warp_incl_scan(nn);
+  S.seg[lane + 1] = incl;
+  if (lane == 0) {
+    S.seg[0] = 0;
+    S.istart[0] = 0;
+  }
+  S.nlow[lane] = (uint8_t)((meta >> 8) & 0xffu);
+  S.cnt[lane] = 0;
+  const uint32_t E = __shfl_sync(full, incl, 31);
+  uint32_t base = 0;
+  if (w0 < n && lane == 0) base = lb.offs[w0];
+  base = __shfl_sync(full, base, 0);
+  __syncwarp();
+
+  // A: overlap test over the warp's flattened entries, compact the touching ones
+  uint32_t qn = 0;
+  for (uint32_t e0 = 0; e0 < E; e0 += 32) {
+    const uint32_t e = e0 + lane;
+    bool hit = false;
+    uint32_t code = 0;
+    int tl = 0;
+    if (e < E) {
+      int lo = 0, hi = 32;
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (S.seg[mid] <= e) lo = mid;
+        else hi = mid;
+      }
+      tl = lo;
+      const uint32_t k = e - S.seg[tl];
+      const uint32_t u = lb.nbr[base + e];
+      const Rec Pt = P[w0 + tl], Pu = P[u];
+      // cheap symmetric pre-test; the exact overlap is taken in phase B
+      hit = Pol::near(Pt, Pu);
+      code = ((uint32_t)tl << 6) | k;
+    }
+    const unsigned m = __ballot_sync(full, hit);
+    if (hit) {
+      S.queue[qn + __popc(m & ((1u << lane) - 1u))] = (uint16_t)code;
+      atomicAdd(&S.cnt[tl], 1u);
+    }
+    qn += __popc(m);
+  }
+  __syncwarp();
+  const uint32_t icl = warp_incl_scan(S.cnt[lane]);
+  S.istart[lane + 1] = icl;
+  __syncwarp();
+  const uint32_t my_a = S.istart[lane], my_b = S.istart[lane + 1];
+
+  // B: contact law for 32 queued contacts at a time, then ordered per-particle sums
+  // (a queued pair found apart by the exact test contributes zero and keeps no
+  // history)
+  uint32_t npair = 0;
+  typename Pol::Acc acc;
+  acc.zero();
+  for (uint32_t i0 = 0; i0 < qn; i0 += 32) {
+    const uint32_t i = i0 + lane;
+    CT c6[6] = {CT(0), CT(0), CT(0), CT(0), CT(0), CT(0)};
+    if (i < qn) {
+      const uint32_t code = S.queue[i];
+      const int tl = (int)(code >> 6);
+      const uint32_t k = code & 63u;
+      const int tt = w0 + tl;
+      const uint32_t e = base + S.seg[tl] + k;
+      const uint32_t u = lb.nbr[e];
+      const bool t_is_i = k >= S.nlow[tl];
+      const Rec Pt = P[tt], Pu = P[u];
+      const Rec Vt = V[tt], Vu = V[u];
+      const Rec Wt = W[tt], Wu = W[u];
+      Hist h = H[e];
+      if (Pol::pair(p, t_is_i, t_is_i ? Pt : Pu, t_is_i ? Pu : Pt, t_is_i ? Vt : Vu,
+                    t_is_i ? Vu : Vt, t_is_i ? Wt : Wu, t_is_i ? Wu : Wt, h, stamp_now,
+                    stamp_new, c6)) {
+        H[e] = h;
+        ++npair;
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 6; ++c) S.contrib[lane][c] = c6[c];
+    __syncwarp();
+    const uint32_t a = my_a > i0 ? my_a : i0;
+    const uint32_t b = my_b < i0 + 32 ? my_b : i0 + 32;
+    for (uint32_t j = a; j < b; ++j) acc.add(S.contrib[j - i0]);
+    __syncwarp();
+  }
+
+  // C: triangle contacts and integration of the lane's own particle
+  uint32_t nmesh = 0;
+  bool disp = false, bad = false;
+  if (valid) Pol::finish(p, sb, ph, lb, mesh, t, (meta >> 16) & 0xffu, acc, stamp_now, stamp_new,
+                         forces, nmesh, disp, bad);
+  count_and_flag(ctl, npair, nmesh, disp, bad);
+}
+
+}  // namespace dem
