@@ -636,3 +636,34 @@ def test_kinetic_reset_with_depth_dependent_stiffness(oracle_mod):
     assert s["v"][0, 2] == pytest.approx(e_n * vn, rel=5e-3)
     assert abs(jt) <= mu * int_fn * (1 + 1e-9)
     assert s["v"][0, 1] - vt == pytest.approx(jt / m, rel=1e-9)
+
+
+def test_hertzian_damping_gives_e_n_exactly_in_the_continuum():
+    # Why the restitution pins can be tight: for the 1-D normal law
+    # m* d'' = -k_n(d) d - c_n(d) d' with k_n = 4/3 E* sqrt(R* d) and
+    # c_n = beta sqrt(5 m* k_n), the exit/entry speed ratio is e_n itself at
+    # any impact speed (solved here by an adaptive ODE integrator, independent
+    # of the oracle's time stepping); a damping factor other than sqrt(5) gives
+    # a different ratio.
+    scipy_integrate = pytest.importorskip("scipy.integrate")
+    R, rho = 1e-3, RHO
+    Rs, ms, Es = R / 2, ph.sphere_mass(rho, R) / 2, E / (2 * (1 - NU ** 2))
+
+    def ratio(e_n, v0, fac=5.0):
+        beta = 1 / math.sqrt(1 + (math.pi / math.log(e_n)) ** 2)
+
+        def f(t, y):
+            d = max(y[0], 0.0)
+            kn = 4 / 3 * Es * math.sqrt(Rs * d)
+            return [y[1], (-kn * y[0] - math.sqrt(fac * ms * kn) * beta * y[1]) / ms]
+
+        ev = lambda t, y: y[0]
+        ev.terminal, ev.direction = True, -1
+        sol = scipy_integrate.solve_ivp(f, [0, 1], [1e-15, v0], events=ev, rtol=1e-12,
+                                        atol=1e-20, max_step=1e-6, method="DOP853")
+        return -sol.y_events[0][0][1] / v0
+
+    for e_n in (0.1, 0.5, 0.9):
+        for v0 in (0.05, 0.5):
+            assert ratio(e_n, v0) == pytest.approx(e_n, abs=1e-8)
+    assert abs(ratio(0.5, 0.5, fac=4.0) - 0.5) > 0.02
