@@ -237,7 +237,8 @@ def bench_ours(a):
                       "rebuilds_in_timed": st["rebuilds"] - st0["rebuilds"],
                       "pair_contacts": st["pair_contacts"], "mesh_contacts": st["mesh_contacts"],
                       "list_entries": st["list_entries"]},
-           "gpu_launches": int(a.steps * st["launches_per_step"]),
+           "gpu_launches": int(a.steps * st["launches_per_step"]
+                               + (st["rebuilds"] - st0["rebuilds"]) * st["launches_per_rebuild"]),
            "roofline": roofline}
     out["clocks"] = clk.summary()
 

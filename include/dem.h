@@ -110,8 +110,8 @@ typedef struct dem_stats {
   int64_t mesh_candidates;/* particle-triangle candidates in the current list */
   int32_t max_list_len;   /* longest per-particle candidate list */
   int32_t status;         /* sticky device status (DEM_OK if none) */
-  int32_t launches_per_step; /* kernels the library launches per time step */
-  int32_t reserved;
+  int32_t launches_per_step;    /* kernels launched in a step without a list rebuild */
+  int32_t launches_per_rebuild; /* additional kernels launched in a step that rebuilds */
 } dem_stats;
 
 typedef struct dem_scene dem_scene;

@@ -48,8 +48,10 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(verbose: bool = False, ptxas_info: bool = False, force: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose: bool = False, ptxas_info: bool = False, force: bool = False,
+          extra_flags=(), build_dir: str = BUILD, lib: str = LIB) -> str:
+    """Compile (if stale) and link libdem.so; extra_flags go to every nvcc call."""
+    os.makedirs(build_dir, exist_ok=True)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")]
     headers.append(os.path.join(INCLUDE, "dem.h"))
     nv = nvcc()
@@ -57,10 +59,11 @@ def build(verbose: bool = False, ptxas_info: bool = False, force: bool = False) 
     objs = []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
-        o = os.path.join(BUILD, src.replace(".cu", ".o"))
+        o = os.path.join(build_dir, src.replace(".cu", ".o"))
         objs.append(o)
         if force or ptxas_info or _stale(o, [s] + headers):
-            extra = (["-Xptxas", "-v"] if ptxas_info else []) + FILE_FLAGS.get(src, [])
+            extra = ((["-Xptxas", "-v"] if ptxas_info else []) + FILE_FLAGS.get(src, [])
+                     + list(extra_flags))
             jobs.append([nv, *_flags(extra), "-c", s, "-o", o])
     outs = []
     if jobs:
@@ -71,18 +74,18 @@ def build(verbose: bool = False, ptxas_info: bool = False, force: bool = False) 
                 outs.append(r.stdout + r.stderr)
                 if r.returncode != 0:
                     raise RuntimeError(f"nvcc failed: {' '.join(j)}\n{r.stdout}\n{r.stderr}")
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if force or jobs or _stale(lib, objs):
+        tmp = lib + f".tmp{os.getpid()}"
         cmd = [nv, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
-        os.replace(tmp, LIB)
+        os.replace(tmp, lib)
     if verbose:
         for o in outs:
             if o.strip():
                 print(o)
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":

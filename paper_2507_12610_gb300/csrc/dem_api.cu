@@ -63,8 +63,9 @@ struct dem_scene {
   double* forces = nullptr;
   Alloc mem;
   cudaGraphExec_t exec1 = nullptr, execG = nullptr;
+  cudaStream_t aux = nullptr;  // captures the conditional rebuild bodies
+  bool conditional_graphs = false;
   bool static_mesh = true;
-  int32_t launches_per_step = 0;
 };
 
 namespace {
@@ -138,14 +139,74 @@ void enqueue_step(dem_scene* s) {
   launch_advance(s->stream, s->ctl, s->p);
 }
 
-int build_graph(dem_scene* s, int nsteps, cudaGraphExec_t* out) {
+// One step inside a stream capture, with the rebuild kernels in the body of a
+// conditional (IF) graph node whose condition a one-thread kernel sets from
+// ctl->rebuild: steps without a rebuild then launch only the step kernels.
+cudaError_t enqueue_step_conditional(dem_scene* s) {
+  if (!s->static_mesh) launch_mesh_pose(s->stream, s->ctl, s->p, s->mesh);
+  cudaStreamCaptureStatus cs;
   cudaGraph_t g = nullptr;
-  DEM_TRY(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
-  for (int i = 0; i < nsteps; ++i) enqueue_step(s);
-  DEM_TRY(cudaStreamEndCapture(s->stream, &g));
-  const cudaError_t e = cudaGraphInstantiate(out, g, 0);
-  cudaGraphDestroy(g);
-  return cuda_status(e);
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(s->stream, &cs, nullptr, &g, nullptr, nullptr, nullptr);
+  if (e != cudaSuccess) return e;
+  cudaGraphConditionalHandle h;
+  e = cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault);
+  if (e != cudaSuccess) return e;
+  launch_decide(s->stream, s->ctl, h);
+  e = cudaStreamGetCaptureInfo(s->stream, &cs, nullptr, &g, &deps, nullptr, &nd);
+  if (e != cudaSuccess) return e;
+  cudaGraphNodeParams np = {};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeIf;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  e = cudaGraphAddNode(&node, g, deps, nullptr, nd, &np);
+  if (e != cudaSuccess) return e;
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  e = cudaStreamBeginCaptureToGraph(s->aux, body, nullptr, nullptr, 0,
+                                    cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  launch_rebuild(s->aux, s->ctl, s->p, s->sb, s->L, s->bb, s->mesh);
+  cudaGraph_t body_out = nullptr;
+  e = cudaStreamEndCapture(s->aux, &body_out);
+  if (e != cudaSuccess) return e;
+  e = cudaStreamUpdateCaptureDependencies(s->stream, &node, nullptr, 1,
+                                          cudaStreamSetCaptureDependencies);
+  if (e != cudaSuccess) return e;
+  launch_step(s->stream, s->ctl, s->p, s->sb, s->L, s->mesh, s->forces);
+  launch_advance(s->stream, s->ctl, s->p);
+  return cudaSuccess;
+}
+
+int build_graph(dem_scene* s, int nsteps, cudaGraphExec_t* out) {
+  // first choice: conditional rebuild bodies; fall back to the plain sequence
+  // (rebuild kernels that return at once) if the driver refuses
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    const bool cond = attempt == 0 && s->aux != nullptr;
+    cudaGraph_t g = nullptr;
+    DEM_TRY(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < nsteps && e == cudaSuccess; ++i) {
+      if (cond) e = enqueue_step_conditional(s);
+      else enqueue_step(s);
+    }
+    const cudaError_t e2 = cudaStreamEndCapture(s->stream, &g);
+    if (e == cudaSuccess && e2 == cudaSuccess) {
+      e = cudaGraphInstantiate(out, g, 0);
+      cudaGraphDestroy(g);
+      if (e == cudaSuccess) {
+        s->conditional_graphs = cond;
+        return DEM_OK;
+      }
+    } else if (g) {
+      cudaGraphDestroy(g);
+    }
+    cudaGetLastError();
+    if (!cond) return cuda_status(e != cudaSuccess ? e : e2);
+  }
+  return DEM_ERR_CUDA;
 }
 
 int read_ctl(dem_scene* s, Ctl* c) {
@@ -349,11 +410,12 @@ int upload_state(dem_scene* s, const double* x, const double* v, const double* w
       split(v ? v[3 * i + 1] : 0.0, V[i].hi.y, V[i].lo.y);
       split(v ? v[3 * i + 2] : 0.0, V[i].hi.z, V[i].lo.z);
       V[i].hi.w = (float)m;
-      V[i].lo.w = 0.f;
+      V[i].lo.w = (float)(1.0 / m);  // inverse mass, for the contact law
       split(w ? w[3 * i] : 0.0, W[i].hi.x, W[i].lo.x);
       split(w ? w[3 * i + 1] : 0.0, W[i].hi.y, W[i].lo.y);
       split(w ? w[3 * i + 2] : 0.0, W[i].hi.z, W[i].lo.z);
-      W[i].hi.w = W[i].lo.w = 0.f;
+      W[i].hi.w = (float)(1.0 / R[i]);  // inverse radius
+      W[i].lo.w = 0.f;
       split(q ? q[4 * i] : 1.0, Q[i].hi.x, Q[i].lo.x);
       split(q ? q[4 * i + 1] : 0.0, Q[i].hi.y, Q[i].lo.y);
       split(q ? q[4 * i + 2] : 0.0, Q[i].hi.z, Q[i].lo.z);
@@ -389,6 +451,7 @@ int upload_state(dem_scene* s, const double* x, const double* v, const double* w
   c.step = step;
   c.rebuild = 1;
   DEM_TRY(cudaMemcpy(s->ctl, &c, sizeof c, cudaMemcpyHostToDevice));
+  launch_set_pose(s->stream, s->ctl, s->p);  // rotation of this step, on the device
   return DEM_OK;
 }
 
@@ -399,6 +462,7 @@ void destroy(dem_scene* s) {
   if (s->stream) cudaStreamSynchronize(s->stream);
   s->mem.release();
   if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+  if (s->aux) cudaStreamDestroy(s->aux);
   delete s;
 }
 
@@ -438,6 +502,10 @@ int dem_scene_create(const dem_params* params, const dem_particles* parts, const
     if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess)
       return fail(DEM_ERR_CUDA);
     s->own_stream = true;
+  }
+  if (cudaStreamCreateWithFlags(&s->aux, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    s->aux = nullptr;
   }
   s->user = *params;
   const int64_t n = parts->n;
@@ -690,10 +758,9 @@ int dem_scene_create(const dem_params* params, const dem_particles* parts, const
         cudaMemcpy(s->mesh.rad, rad.data(), s->nt * sizeof(double), cudaMemcpyHostToDevice))
       return fail(DEM_ERR_CUDA);
   }
-  // kernels per step: mesh pose, rebuild (prep, clear, count, 3 scan, scatter,
-  // cell sort, permute, [mesh: clear, count, 3 scan, check, clear, fill, sort],
-  // list build, 3 scan, compact, end), step, advance
-  s->launches_per_step = (s->static_mesh ? 0 : 1) + 15 + (has_mesh ? 9 : 0) + 2;
+  // kernels per step: mesh pose, [decide], rebuild (prep, clear, count, 3 scan,
+  // scatter, cell sort, permute, [mesh: clear, count, 3 scan, check, clear, fill,
+  // sort], list build, 3 scan, compact, end), step, advance -- see dem_get_stats
   rc = upload_state(s, parts->x, parts->v, parts->w, parts->q, parts->R, 0);
   if (rc != DEM_OK) return fail(rc);
   // pose at step 0 (a static mesh keeps it)
@@ -858,8 +925,15 @@ int dem_get_stats(dem_scene* s, dem_stats* out) {
   out->mesh_candidates = c.mesh_candidates;
   out->max_list_len = (int32_t)c.max_list_len;
   out->status = (int32_t)c.status;
-  out->launches_per_step = s->launches_per_step;
-  out->reserved = 0;
+  const int32_t rebuild_launches = 15 + (s->nt > 0 ? 9 : 0);
+  const int32_t base = (s->static_mesh ? 0 : 1) + 2;
+  if (s->conditional_graphs) {
+    out->launches_per_step = base + 1;
+    out->launches_per_rebuild = rebuild_launches;
+  } else {
+    out->launches_per_step = base + rebuild_launches;
+    out->launches_per_rebuild = 0;
+  }
   return DEM_OK;
 }
 
@@ -984,6 +1058,7 @@ int dem_load(dem_scene* s, const void* buf, size_t len) {
   c.step = step;
   c.rebuild = 1;
   DEM_TRY(cudaMemcpy(s->ctl, &c, sizeof c, cudaMemcpyHostToDevice));
+  launch_set_pose(s->stream, s->ctl, s->p);
   launch_mesh_pose(s->stream, s->ctl, s->p, s->mesh);
   DEM_TRY(cudaStreamSynchronize(s->stream));
   return DEM_OK;

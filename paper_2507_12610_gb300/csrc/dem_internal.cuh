@@ -28,6 +28,7 @@ struct Ctl {
   int64_t step;         // steps completed
   int64_t rebuilds;
   double mesh_angle_ref;  // mesh rotation angle at the last rebuild
+  double rot_c, rot_s;    // cos / sin of the mesh rotation angle of the current step
   uint32_t pair_contacts;  // touching directed pair entries, this step (accumulating)
   uint32_t mesh_contacts;
   uint32_t pair_contacts_last;  // ... of the last completed step
@@ -88,8 +89,8 @@ struct __align__(32) F8 {
 };
 struct StateM {
   F8* P;  // X - origin (shifted, hi/lo), R (hi/lo)
-  F8* V;  // v (hi/lo); hi.w = m
-  F8* W;  // w (hi/lo)
+  F8* V;  // v (hi/lo); hi.w = m, lo.w = 1/m
+  F8* W;  // w (hi/lo); hi.w = 1/R
   F8* Q;  // q (hi/lo)
 };
 
@@ -176,6 +177,10 @@ void launch_rebuild(cudaStream_t st, Ctl* ctl, const Params& p, StateBufs sb, Li
 void launch_step(cudaStream_t st, Ctl* ctl, const Params& p, StateBufs sb, Lists L,
                  MeshDev mesh, double* forces);
 void launch_advance(cudaStream_t st, Ctl* ctl, const Params& p);
+// Sets ctl->rot_c / rot_s for the step in the control block.
+void launch_set_pose(cudaStream_t st, Ctl* ctl, const Params& p);
+// Sets a graph IF-condition from ctl->rebuild (inside a captured graph).
+void launch_decide(cudaStream_t st, const Ctl* ctl, cudaGraphConditionalHandle h);
 
 // Scan of a u32 array (exclusive) on the device; early-exits unless ctl->rebuild.
 void launch_scan(cudaStream_t st, const Ctl* ctl, const uint32_t* in, uint32_t* out, int64_t n,

@@ -28,33 +28,38 @@ namespace {
 
 __global__ void k_mesh_pose(const Ctl* ctl, Params p, MeshDev mesh) {
   if (ctl->status) return;
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= mesh.nt) return;
-  const double wn = p.omega_norm;
-  double c = 1.0, s = 0.0;
-  V3<double> ax = mk(0.0, 0.0, 0.0);
-  const V3<double> ctr = mk(p.mesh_center[0], p.mesh_center[1], p.mesh_center[2]);
-  if (wn > 0.0) {
-    const double th = wn * ((double)ctl->step * p.dt);
-    c = cos(th);
-    s = sin(th);
-    ax = (1.0 / wn) * mk(p.mesh_omega[0], p.mesh_omega[1], p.mesh_omega[2]);
-  }
+  const int slot = blockIdx.x * blockDim.x + threadIdx.x;  // triangle-vertex slot
+  if (slot >= 3 * mesh.nt) return;
+  const int k = slot / 3, j = slot - 3 * k;
   const int4 tv = mesh.tri[k];
-  const int idx[3] = {tv.x, tv.y, tv.z};
-#pragma unroll
-  for (int j = 0; j < 3; ++j) {
-    const D4 r0 = mesh.ref[idx[j]];
-    V3<double> pos = xyz(r0);
-    if (wn > 0.0) {
-      const V3<double> r = pos - ctr;
-      const V3<double> rr = c * r + s * cross(ax, r) + (dot(ax, r) * (1.0 - c)) * ax;
-      pos = ctr + rr;
-    }
-    mesh.cur[3 * k + j] = make_D4(pos.x, pos.y, pos.z, j == 0 ? mesh.rad[k] : 0.0);
-    mesh.curf[3 * k + j] = make_float4((float)(pos.x - p.origin[0]), (float)(pos.y - p.origin[1]),
-                                       (float)(pos.z - p.origin[2]), 0.f);
+  const D4 r0 = mesh.ref[j == 0 ? tv.x : (j == 1 ? tv.y : tv.z)];
+  V3<double> pos = xyz(r0);
+  const double wn = p.omega_norm;
+  if (wn > 0.0) {
+    const double c = ctl->rot_c, s = ctl->rot_s;
+    const V3<double> ax = (1.0 / wn) * mk(p.mesh_omega[0], p.mesh_omega[1], p.mesh_omega[2]);
+    const V3<double> ctr = mk(p.mesh_center[0], p.mesh_center[1], p.mesh_center[2]);
+    const V3<double> r = pos - ctr;
+    const V3<double> rr = c * r + s * cross(ax, r) + (dot(ax, r) * (1.0 - c)) * ax;
+    pos = ctr + rr;
   }
+  mesh.cur[slot] = make_D4(pos.x, pos.y, pos.z, j == 0 ? mesh.rad[k] : 0.0);
+  mesh.curf[slot] = make_float4((float)(pos.x - p.origin[0]), (float)(pos.y - p.origin[1]),
+                                (float)(pos.z - p.origin[2]), 0.f);
+}
+
+// Rotation of the mesh at the control block's step (after a host upload); the
+// same expression k_advance uses, so a resumed run sees the same bits.
+__global__ void k_set_pose(Ctl* ctl, Params p) {
+  const double th = p.omega_norm * ((double)ctl->step * p.dt);
+  ctl->rot_c = cos(th);
+  ctl->rot_s = sin(th);
+}
+
+// ---- graph condition: run the rebuild body of this step or skip it ----------
+
+__global__ void k_decide(const Ctl* ctl, cudaGraphConditionalHandle h) {
+  cudaGraphSetConditional(h, (ctl->rebuild != 0u && ctl->status == 0u) ? 1u : 0u);
 }
 
 // ---- end of step: flip buffers, count, decide the next rebuild -------------
@@ -72,6 +77,8 @@ __global__ void k_advance(Ctl* ctl, Params p) {
   bool mesh_moved = false;
   if (p.omega_norm > 0.0) {
     const double th = p.omega_norm * ((double)ctl->step * p.dt);
+    ctl->rot_c = cos(th);  // pose of the next step
+    ctl->rot_s = sin(th);
     const double chord = 2.0 * p.mesh_rmax * fabs(sin(0.5 * (th - ctl->mesh_angle_ref)));
     mesh_moved = chord >= (double)p.half_skin_trigger;
   }
@@ -100,8 +107,21 @@ __device__ __forceinline__ void acc(float& hi, float& lo, float b) {
   lo = s.lo;
 }
 
+#ifndef DEM_MIXED_MIN_BLOCKS
+#define DEM_MIXED_MIN_BLOCKS 6
+#endif
+
+// sin x: Taylor polynomial to x^7 for |x| < 1/16 (the first omitted term is
+// below 1e-15 relative, far under FP32 rounding), sinf otherwise.  The
+// rotation angles of one step are tiny.
+__device__ __forceinline__ float sin_small(float x) {
+  if (fabsf(x) >= 0.0625f) return sinf(x);
+  const float x2 = x * x;
+  return x * (1.f - x2 * (1.f / 6.f) * (1.f - x2 * (1.f / 20.f) * (1.f - x2 * (1.f / 42.f))));
+}
+
 struct MixedPolicy {
-  static constexpr int kMinBlocks = 5;  // resident blocks per SM the registers must allow
+  static constexpr int kMinBlocks = DEM_MIXED_MIN_BLOCKS;  // resident blocks per SM
   using Rec = F8;
   using Hist = HistM;
   using T = float;
@@ -178,8 +198,8 @@ struct MixedPolicy {
     const LawConst<float> cpp{p.f_Es_pp, p.f_Gs_pp, p.f_beta, p.f_mu_s, p.f_mu_r, p.f_mu_t,
                               p.f_dt};
     const float Ri = Pi.hi.w + Pi.lo.w, Rj = Pj.hi.w + Pj.lo.w;
-    const float Rs = 1.f / (1.f / Ri + 1.f / Rj);
-    const float ms = 1.f / (1.f / Vi.hi.w + 1.f / Vj.hi.w);
+    const float Rs = 1.f / (Wi.hi.w + Wj.hi.w);  // records carry 1/R and 1/m
+    const float ms = 1.f / (Vi.lo.w + Vj.lo.w);
     const float ri = Ri - 0.5f * g.delta, rj = Rj - 0.5f * g.delta;
     V3<float> us = mk(0.f, 0.f, 0.f), ur = us;
     float ut = 0.f;
@@ -209,16 +229,13 @@ struct MixedPolicy {
   static __device__ __forceinline__ void finish(const Params& p, const StateBufs& sb,
                                                 uint32_t ph, const ListBuf& lb,
                                                 const MeshDev& mesh, int t, uint32_t ntc_u,
+                                                const F8& Pt, const F8& Vt, const F8& Wt,
                                                 Acc& sums, uint32_t stamp_now, uint32_t stamp_new,
                                                 double* forces, uint32_t& nmesh, bool& disp,
                                                 bool& bad) {
     const int n = p.n;
     const int ntc = (int)ntc_u;
-    const F8* P = static_cast<const F8*>(sb.P[ph]);
-    const F8* V = static_cast<const F8*>(sb.V[ph]);
-    const F8* W = static_cast<const F8*>(sb.W[ph]);
     const F8* Q = static_cast<const F8*>(sb.Q[ph]);
-    const F8 Pt = P[t], Vt = V[t], Wt = W[t];
     const float Rt = Pt.hi.w + Pt.lo.w;
     Acc3& F = sums.F;
     Acc3& T = sums.T;
@@ -290,7 +307,7 @@ struct MixedPolicy {
     const float gi = 10.f / 3.f * ci;
     const float dt = p.f_dt;
     const V3<float> v0 = sum3(Vt), w0 = sum3(Wt);
-    const float im = 1.f / mass, iI = 1.f / I;
+    const float im = Vt.lo.w, iI = 1.f / I;
     const V3<float> a = mk((F.hx + F.lx) * im + p.f_g[0] - ci * v0.x,
                            (F.hy + F.ly) * im + p.f_g[1] - ci * v0.y,
                            (F.hz + F.lz) * im + p.f_g[2] - ci * v0.z);
@@ -309,8 +326,8 @@ struct MixedPolicy {
     const float wn = sqrtf(dot(w0, w0));
     if (wn > 0.f) {
       const float phi = 0.5f * dt * wn;
-      const float sh = sinf(0.5f * phi);
-      const float sp = sinf(phi);
+      const float sh = sin_small(0.5f * phi);
+      const float sp = sin_small(phi);
       const float r[4] = {-2.f * sh * sh, sp * w0.x / wn, sp * w0.y / wn, sp * w0.z / wn};
       const float qh[4] = {Qn.hi.x + Qn.lo.x, Qn.hi.y + Qn.lo.y, Qn.hi.z + Qn.lo.z,
                            Qn.hi.w + Qn.lo.w};
@@ -324,8 +341,8 @@ struct MixedPolicy {
     const float an = sqrtf(dot(al, al));
     if (an > 0.f) {
       const float th = (0.5f * dt) * (0.5f * dt) * an;
-      const float sh = sinf(0.5f * th);
-      const float st = sinf(th);
+      const float sh = sin_small(0.5f * th);
+      const float st = sin_small(th);
       const float r[4] = {-2.f * sh * sh, st * al.x / an, st * al.y / an, st * al.z / an};
       const float qh[4] = {Qn.hi.x + Qn.lo.x, Qn.hi.y + Qn.lo.y, Qn.hi.z + Qn.lo.z,
                            Qn.hi.w + Qn.lo.w};
@@ -365,7 +382,7 @@ struct MixedPolicy {
 
 void launch_mesh_pose(cudaStream_t st, const Ctl* ctl, const Params& p, MeshDev mesh) {
   if (mesh.nt <= 0) return;
-  k_mesh_pose<<<(unsigned)((mesh.nt + 127) / 128), 128, 0, st>>>(ctl, p, mesh);
+  k_mesh_pose<<<(unsigned)((3 * mesh.nt + 127) / 128), 128, 0, st>>>(ctl, p, mesh);
 }
 
 void launch_step(cudaStream_t st, Ctl* ctl, const Params& p, StateBufs sb, Lists L,
@@ -375,6 +392,14 @@ void launch_step(cudaStream_t st, Ctl* ctl, const Params& p, StateBufs sb, Lists
                                0, st>>>(ctl, p, sb, L, mesh, forces);
   else
     launch_step_fp64(st, ctl, p, sb, L, mesh, forces);
+}
+
+void launch_set_pose(cudaStream_t st, Ctl* ctl, const Params& p) {
+  k_set_pose<<<1, 1, 0, st>>>(ctl, p);
+}
+
+void launch_decide(cudaStream_t st, const Ctl* ctl, cudaGraphConditionalHandle h) {
+  k_decide<<<1, 1, 0, st>>>(ctl, h);
 }
 
 void launch_advance(cudaStream_t st, Ctl* ctl, const Params& p) {

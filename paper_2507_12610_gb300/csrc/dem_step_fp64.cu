@@ -20,8 +20,12 @@ namespace {
 // DEM_FP64
 // ============================================================================
 
+#ifndef DEM_FP64_MIN_BLOCKS
+#define DEM_FP64_MIN_BLOCKS 4
+#endif
+
 struct Fp64Policy {
-  static constexpr int kMinBlocks = 4;  // resident blocks per SM the registers must allow
+  static constexpr int kMinBlocks = DEM_FP64_MIN_BLOCKS;  // resident blocks per SM
   using Rec = D4;
   using Hist = HistD;
   using T = double;
@@ -105,16 +109,13 @@ struct Fp64Policy {
   static __device__ __forceinline__ void finish(const Params& p, const StateBufs& sb,
                                                 uint32_t ph, const ListBuf& lb,
                                                 const MeshDev& mesh, int t, uint32_t ntc_u,
+                                                const D4& Pt, const D4& Vt, const D4& Wt,
                                                 Acc& sums, uint32_t stamp_now,
                                                 uint32_t stamp_new, double* forces,
                                                 uint32_t& nmesh, bool& disp, bool& bad) {
     const int n = p.n;
     const int ntc = (int)ntc_u;
-    const D4* P = static_cast<const D4*>(sb.P[ph]);
-    const D4* V = static_cast<const D4*>(sb.V[ph]);
-    const D4* W = static_cast<const D4*>(sb.W[ph]);
     const D4* Q = static_cast<const D4*>(sb.Q[ph]);
-    const D4 Pt = P[t], Vt = V[t], Wt = W[t];
     V3<double>& F = sums.F;
     V3<double>& T = sums.T;
     // particle-triangle contacts

@@ -104,9 +104,9 @@ k_step_warp(Ctl* ctl, Params p, StateBufs sb, Lists L, MeshDev mesh, double* for
       tl = lo;
       const uint32_t k = e - S.seg[tl];
       const uint32_t u = lb.nbr[base + e];
-      const Rec Pt = P[w0 + tl], Pu = P[u];
+      const Rec Pu = P[u];
       // cheap symmetric pre-test; the exact overlap is taken in phase B
-      hit = Pol::near(Pt, Pu);
+      hit = Pol::near(P[w0 + tl], Pu);
       code = ((uint32_t)tl << 6) | k;
     }
     const unsigned m = __ballot_sync(full, hit);
@@ -135,13 +135,12 @@ k_step_warp(Ctl* ctl, Params p, StateBufs sb, Lists L, MeshDev mesh, double* for
       const uint32_t code = S.queue[i];
       const int tl = (int)(code >> 6);
       const uint32_t k = code & 63u;
-      const int tt = w0 + tl;
       const uint32_t e = base + S.seg[tl] + k;
       const uint32_t u = lb.nbr[e];
       const bool t_is_i = k >= S.nlow[tl];
-      const Rec Pt = P[tt], Pu = P[u];
-      const Rec Vt = V[tt], Vu = V[u];
-      const Rec Wt = W[tt], Wu = W[u];
+      const Rec Pt = P[w0 + tl], Pu = P[u];
+      const Rec Vt = V[w0 + tl], Vu = V[u];
+      const Rec Wt = W[w0 + tl], Wu = W[u];
       Hist h = H[e];
       if (Pol::pair(p, t_is_i, t_is_i ? Pt : Pu, t_is_i ? Pu : Pt, t_is_i ? Vt : Vu,
                     t_is_i ? Vu : Vt, t_is_i ? Wt : Wu, t_is_i ? Wu : Wt, h, stamp_now,
@@ -162,8 +161,10 @@ k_step_warp(Ctl* ctl, Params p, StateBufs sb, Lists L, MeshDev mesh, double* for
   // C: triangle contacts and integration of the lane's own particle
   uint32_t nmesh = 0;
   bool disp = false, bad = false;
-  if (valid) Pol::finish(p, sb, ph, lb, mesh, t, (meta >> 16) & 0xffu, acc, stamp_now, stamp_new,
-                         forces, nmesh, disp, bad);
+  if (valid)
+    Pol::finish(p, sb, ph, lb, mesh, t, (meta >> 16) & 0xffu, P[t], V[t],
+                W[t], acc, stamp_now, stamp_new, forces, nmesh, disp, bad);
+
   count_and_flag(ctl, npair, nmesh, disp, bad);
 }
 

@@ -14,7 +14,7 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libdem.so")
+LIB_PATH = os.environ.get("DEM_LIB_PATH") or os.path.join(HERE, "libdem.so")
 
 DEM_OK = 0
 DEM_ERR_INVALID = 1
@@ -61,7 +61,7 @@ class dem_stats(ctypes.Structure):
     _fields_ = [("steps", _I64), ("rebuilds", _I64), ("pair_contacts", _I64),
                 ("mesh_contacts", _I64), ("list_entries", _I64), ("mesh_candidates", _I64),
                 ("max_list_len", _I32), ("status", _I32), ("launches_per_step", _I32),
-                ("reserved", _I32)]
+                ("launches_per_rebuild", _I32)]
 
 
 class DemError(RuntimeError):
