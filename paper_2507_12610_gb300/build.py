@@ -35,8 +35,8 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found")
 
 
-def _flags(extra=()):
-    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-I", INCLUDE, "-I", CSRC,
+def _flags(extra=(), csrc=CSRC):
+    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-I", INCLUDE, "-I", csrc,
                    "-Xcompiler", "-fPIC,-ffp-contract=off", "--expt-relaxed-constexpr",
                    *extra]
 
@@ -49,22 +49,24 @@ def _stale(target: str, deps) -> bool:
 
 
 def build(verbose: bool = False, ptxas_info: bool = False, force: bool = False,
-          extra_flags=(), build_dir: str = BUILD, lib: str = LIB) -> str:
+          extra_flags=(), build_dir: str = BUILD, lib: str = LIB, csrc: str = CSRC) -> str:
     """Compile (if stale) and link libdem.so; extra_flags go to every nvcc call."""
     os.makedirs(build_dir, exist_ok=True)
-    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")]
+    headers = [os.path.join(csrc, f) for f in os.listdir(csrc) if f.endswith(".cuh")]
     headers.append(os.path.join(INCLUDE, "dem.h"))
     nv = nvcc()
     jobs = []
     objs = []
     for src in SOURCES:
-        s = os.path.join(CSRC, src)
+        if not os.path.exists(os.path.join(csrc, src)):
+            continue
+        s = os.path.join(csrc, src)
         o = os.path.join(build_dir, src.replace(".cu", ".o"))
         objs.append(o)
         if force or ptxas_info or _stale(o, [s] + headers):
             extra = ((["-Xptxas", "-v"] if ptxas_info else []) + FILE_FLAGS.get(src, [])
                      + list(extra_flags))
-            jobs.append([nv, *_flags(extra), "-c", s, "-o", o])
+            jobs.append([nv, *_flags(extra, csrc), "-c", s, "-o", o])
     outs = []
     if jobs:
         with cf.ThreadPoolExecutor(max_workers=len(jobs)) as ex:

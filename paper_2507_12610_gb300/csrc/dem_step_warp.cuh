@@ -4,13 +4,16 @@
 // contiguous in the CSR list, so:
 //   A. the lanes walk the warp's flattened entries 32 at a time (coalesced
 //      list reads), pre-test each pair for overlap with a cheap conservative
-//      test, and append the candidates to a per-warp queue in shared memory;
-//      the queue is in entry order, so each particle's contacts are contiguous
-//      and in ascending partner index;
+//      test, and append the candidates (entry code and partner slot) to a
+//      per-warp queue in shared memory, prefetching their history records
+//      into L2; the queue is in entry order, so each particle's contacts are
+//      contiguous and in ascending partner index;
 //   B. the lanes evaluate the contact law for 32 queued contacts at a time
 //      (all lanes busy), write the friction history, and park each contact's
 //      force/torque on its own particle in shared memory; then every lane adds
 //      the parked contributions of its own particle in queue order;
+//      A and B alternate in rounds whenever the queue is full, which keeps
+//      the order and bounds the shared memory;
 //   C. each lane finishes its particle: triangle contacts, integration.
 // The sum of every particle is therefore taken in exactly the order of the
 // per-particle loop (ascending partner caller index, then triangle index),
@@ -25,7 +28,7 @@ namespace dem {
 
 constexpr int kStepWarps = 4;             // warps per block
 constexpr int kStepThreads = 32 * kStepWarps;
-constexpr int kQueueMax = 32 * 64;        // a particle has at most 64 list entries
+constexpr int kQueueMax = 512;            // queued contacts per warp and round
 
 template <typename CT>
 struct WarpScratch {
@@ -33,7 +36,8 @@ struct WarpScratch {
   uint32_t istart[33];  // queued-contact prefix of the warp's particles
   uint32_t cnt[32];
   uint8_t nlow[32];
-  uint16_t queue[kQueueMax];  // (particle << 6) | entry
+  uint16_t qcode[kQueueMax];  // (particle << 6) | entry
+  uint32_t qslot[kQueueMax];  // partner slot
   CT contrib[32][6];
 };
 
@@ -80,83 +84,88 @@ k_step_warp(Ctl* ctl, Params p, StateBufs sb, Lists L, MeshDev mesh, double* for
     S.istart[0] = 0;
   }
   S.nlow[lane] = (uint8_t)((meta >> 8) & 0xffu);
-  S.cnt[lane] = 0;
   const uint32_t E = __shfl_sync(full, incl, 31);
   uint32_t base = 0;
   if (w0 < n && lane == 0) base = lb.offs[w0];
   base = __shfl_sync(full, base, 0);
-  __syncwarp();
 
-  // A: overlap test over the warp's flattened entries, compact the touching ones
-  uint32_t qn = 0;
-  for (uint32_t e0 = 0; e0 < E; e0 += 32) {
-    const uint32_t e = e0 + lane;
-    bool hit = false;
-    uint32_t code = 0;
-    int tl = 0;
-    if (e < E) {
-      int lo = 0, hi = 32;
-      while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (S.seg[mid] <= e) lo = mid;
-        else hi = mid;
-      }
-      tl = lo;
-      const uint32_t k = e - S.seg[tl];
-      const uint32_t u = lb.nbr[base + e];
-      const Rec Pu = P[u];
-      // cheap symmetric pre-test; the exact overlap is taken in phase B
-      hit = Pol::near(P[w0 + tl], Pu);
-      code = ((uint32_t)tl << 6) | k;
-    }
-    const unsigned m = __ballot_sync(full, hit);
-    if (hit) {
-      S.queue[qn + __popc(m & ((1u << lane) - 1u))] = (uint16_t)code;
-      atomicAdd(&S.cnt[tl], 1u);
-    }
-    qn += __popc(m);
-  }
-  __syncwarp();
-  const uint32_t icl = warp_incl_scan(S.cnt[lane]);
-  S.istart[lane + 1] = icl;
-  __syncwarp();
-  const uint32_t my_a = S.istart[lane], my_b = S.istart[lane + 1];
-
-  // B: contact law for 32 queued contacts at a time, then ordered per-particle sums
-  // (a queued pair found apart by the exact test contributes zero and keeps no
-  // history)
   uint32_t npair = 0;
   typename Pol::Acc acc;
   acc.zero();
-  for (uint32_t i0 = 0; i0 < qn; i0 += 32) {
-    const uint32_t i = i0 + lane;
-    CT c6[6] = {CT(0), CT(0), CT(0), CT(0), CT(0), CT(0)};
-    if (i < qn) {
-      const uint32_t code = S.queue[i];
-      const int tl = (int)(code >> 6);
-      const uint32_t k = code & 63u;
-      const uint32_t e = base + S.seg[tl] + k;
-      const uint32_t u = lb.nbr[e];
-      const bool t_is_i = k >= S.nlow[tl];
-      const Rec Pt = P[w0 + tl], Pu = P[u];
-      const Rec Vt = V[w0 + tl], Vu = V[u];
-      const Rec Wt = W[w0 + tl], Wu = W[u];
-      Hist h = H[e];
-      if (Pol::pair(p, t_is_i, t_is_i ? Pt : Pu, t_is_i ? Pu : Pt, t_is_i ? Vt : Vu,
-                    t_is_i ? Vu : Vt, t_is_i ? Wt : Wu, t_is_i ? Wu : Wt, h, stamp_now,
-                    stamp_new, c6)) {
-        H[e] = h;
-        ++npair;
+  uint32_t e0 = 0;
+  do {
+    S.cnt[lane] = 0;
+    __syncwarp();
+    // A: overlap pre-test over the warp's flattened entries, queue candidates
+    uint32_t qn = 0;
+    for (; e0 < E && qn + 32 <= (uint32_t)kQueueMax; e0 += 32) {
+      const uint32_t e = e0 + lane;
+      bool hit = false;
+      uint32_t code = 0, u = 0;
+      int tl = 0;
+      if (e < E) {
+        int lo = 0, hi = 32;
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (S.seg[mid] <= e) lo = mid;
+          else hi = mid;
+        }
+        tl = lo;
+        const uint32_t k = e - S.seg[tl];
+        u = lb.nbr[base + e];
+        // cheap symmetric pre-test; the exact overlap is taken in phase B
+        hit = Pol::near(P[w0 + tl], P[u]);
+        code = ((uint32_t)tl << 6) | k;
+        if (hit) asm volatile("prefetch.global.L2 [%0];" ::"l"(H + base + e));
       }
+      const unsigned m = __ballot_sync(full, hit);
+      if (hit) {
+        const uint32_t pos = qn + __popc(m & ((1u << lane) - 1u));
+        S.qcode[pos] = (uint16_t)code;
+        S.qslot[pos] = u;
+        atomicAdd(&S.cnt[tl], 1u);
+      }
+      qn += __popc(m);
     }
+    __syncwarp();
+    const uint32_t icl = warp_incl_scan(S.cnt[lane]);
+    S.istart[lane + 1] = icl;
+    __syncwarp();
+    const uint32_t my_a = S.istart[lane], my_b = S.istart[lane + 1];
+
+    // B: contact law for 32 queued contacts at a time, then ordered
+    // per-particle sums (a queued pair found apart by the exact test
+    // contributes zero and keeps no history)
+    for (uint32_t i0 = 0; i0 < qn; i0 += 32) {
+      const uint32_t i = i0 + lane;
+      CT c6[6] = {CT(0), CT(0), CT(0), CT(0), CT(0), CT(0)};
+      if (i < qn) {
+        const uint32_t code = S.qcode[i];
+        const uint32_t u = S.qslot[i];
+        const int tl = (int)(code >> 6);
+        const uint32_t k = code & 63u;
+        const uint32_t e = base + S.seg[tl] + k;
+        const bool t_is_i = k >= S.nlow[tl];
+        const Rec Pt = P[w0 + tl], Pu = P[u];
+        const Rec Vt = V[w0 + tl], Vu = V[u];
+        const Rec Wt = W[w0 + tl], Wu = W[u];
+        Hist h = H[e];
+        if (Pol::pair(p, t_is_i, t_is_i ? Pt : Pu, t_is_i ? Pu : Pt, t_is_i ? Vt : Vu,
+                      t_is_i ? Vu : Vt, t_is_i ? Wt : Wu, t_is_i ? Wu : Wt, h, stamp_now,
+                      stamp_new, c6)) {
+          H[e] = h;
+          ++npair;
+        }
+      }
 #pragma unroll
-    for (int c = 0; c < 6; ++c) S.contrib[lane][c] = c6[c];
-    __syncwarp();
-    const uint32_t a = my_a > i0 ? my_a : i0;
-    const uint32_t b = my_b < i0 + 32 ? my_b : i0 + 32;
-    for (uint32_t j = a; j < b; ++j) acc.add(S.contrib[j - i0]);
-    __syncwarp();
-  }
+      for (int c = 0; c < 6; ++c) S.contrib[lane][c] = c6[c];
+      __syncwarp();
+      const uint32_t a = my_a > i0 ? my_a : i0;
+      const uint32_t b = my_b < i0 + 32 ? my_b : i0 + 32;
+      for (uint32_t jj = a; jj < b; ++jj) acc.add(S.contrib[jj - i0]);
+      __syncwarp();
+    }
+  } while (e0 < E);
 
   // C: triangle contacts and integration of the lane's own particle
   uint32_t nmesh = 0;
