@@ -115,6 +115,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(x: float, world: int, device: str = "cpu") -> float:
+    """Largest value over the ranks of the process group (x itself if alone)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(n_per_rank: int, steps: int, elapsed_max: float, world: int) -> float:
+    """Whole-job particle-steps/s of `world` replicas timed by the slowest."""
+    return world * n_per_rank * steps / elapsed_max
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -195,13 +211,8 @@ def bench_ours(a):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        import torch.distributed as dist
-        t = torch.tensor([x], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    def rank_max(x: float) -> float:
+        return max_over_ranks(x, world, "cuda")
 
     prec = dem.DEM_MIXED if a.precision == "mixed" else dem.DEM_FP64
     s = drum_workload(a.n, seed=5 + rank)
@@ -234,9 +245,9 @@ def bench_ours(a):
     rc = sc.synchronize()
     barrier()
     assert rc == 0, f"timed run failed: {dem.status_string(rc)}"
-    elapsed = max_over_ranks(e0.elapsed_time(e1) / 1e3)
+    elapsed = rank_max(e0.elapsed_time(e1) / 1e3)
     st = sc.stats()
-    value = world * n * a.steps / elapsed
+    value = aggregate_rate(n, a.steps, elapsed, world)
     ms_per_step = elapsed / a.steps * 1e3
 
     # per-phase device times with CUDA events on the scene stream
@@ -289,9 +300,9 @@ def bench_ours(a):
         e1.record(strm)
         e1.synchronize()
         rc64 = sd.synchronize()
-        t64 = max_over_ranks(e0.elapsed_time(e1) / 1e3)
+        t64 = rank_max(e0.elapsed_time(e1) / 1e3)
         ph64 = sd.step_timed(max(5, k64 // 4))
-        out["fp64"] = {"value": world * n * k64 / t64, "ms_per_step": t64 / k64 * 1e3,
+        out["fp64"] = {"value": aggregate_rate(n, k64, t64, world), "ms_per_step": t64 / k64 * 1e3,
                        "steps": k64, "status": rc64,
                        "step_kernel_ms": ph64[2] / max(5, k64 // 4),
                        "bound": "alu (FP64 pipe)"}
@@ -309,11 +320,11 @@ def bench_ours(a):
         for _ in range(frames):
             se.step(a.frame)
             rce = se.read_state_into(x, v, w, q)
-        t_e2e = max_over_ranks(time.perf_counter() - t0)
+        t_e2e = rank_max(time.perf_counter() - t0)
         se.close()
         steps_e2e = frames * a.frame
         rec = 32
-        out["e2e"] = {"value": world * n * steps_e2e / t_e2e, "unit": UNIT,
+        out["e2e"] = {"value": aggregate_rate(n, steps_e2e, t_e2e, world), "unit": UNIT,
                       "h2d_bytes_per_step": int(n * 14 * 8 / steps_e2e),
                       "d2h_bytes_per_step": int(frames * n * (4 * rec + 4) / steps_e2e),
                       "status": rce, "frames": frames, "steps_per_frame": a.frame}

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -183,8 +184,12 @@ cudaError_t enqueue_step_conditional(dem_scene* s) {
 int build_graph(dem_scene* s, int nsteps, cudaGraphExec_t* out) {
   // first choice: conditional rebuild bodies; fall back to the plain sequence
   // (rebuild kernels that return at once) if the driver refuses
+  // DEM_GRAPH_CONDITIONAL=0 in the environment keeps every rebuild kernel a
+  // plain graph node (profilers cannot see kernels of conditional graphs)
+  const char* env = std::getenv("DEM_GRAPH_CONDITIONAL");
+  const bool allow_cond = !(env && env[0] == '0');
   for (int attempt = 0; attempt < 2; ++attempt) {
-    const bool cond = attempt == 0 && s->aux != nullptr;
+    const bool cond = attempt == 0 && s->aux != nullptr && allow_cond;
     cudaGraph_t g = nullptr;
     DEM_TRY(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
