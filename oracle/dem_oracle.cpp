@@ -21,9 +21,11 @@
 //     sets f_t = mu_t |f_n| sign(f_t).
 //   * Contact lifetime (Sec. 3.2): a contact exists in a step iff delta >= 0; its
 //     history starts at zero and is dropped on the first step with delta < 0.
-//   * Mesh elements (Sec. 2.2, 3.3): R_j = E_j = m_j = infinity, so R* = R_i,
-//     m* = m_i; the element radius enters only delta.  Each touching triangle is
-//     an independent contact (ghost collisions are kept, Sec. 3.3).
+//   * Mesh elements (Sec. 2.2, 3.3): points, segments, triangles and
+//     rectangles, each with a radius R_j >= 0 (rounded edges).  R_j = E_j =
+//     m_j = infinity in the contact law, so R* = R_i, m* = m_i; the element
+//     radius enters only delta.  Each touching element is an independent
+//     contact (ghost collisions are kept, Sec. 3.3).
 //   * Rotating mesh (not in the paper, which keeps walls static): the mesh turns
 //     rigidly with angular velocity Omega about `mesh_center`; at step n its
 //     vertices are the reference vertices rotated by angle |Omega| n dt.  The
@@ -100,10 +102,10 @@ struct Scene {
   int64_t n = 0;
   std::vector<double> R, x, v, w, q;  // R[n], x/v/w[3n], q[4n] (scalar first)
   std::vector<double> F, T;           // contact force / torque sums of the last step
-  int64_t nv = 0, nt = 0;
+  int64_t nv = 0, nt = 0;             // vertices, mesh elements
   std::vector<double> vert0;          // reference vertices [3 nv]
-  std::vector<int32_t> tri;           // [3 nt]
-  std::vector<double> tri_radius;     // [nt]
+  std::vector<int32_t> tri;           // [4 nt] vertex indices, -1 pads (1..4 vertices)
+  std::vector<double> tri_radius;     // [nt] element radius
   std::map<Key, Hist> hist;
   int64_t step_count = 0;
   int64_t degenerate = 0;  // contacts skipped because d == 0
@@ -156,6 +158,42 @@ V3 closest_on_triangle(V3 p, V3 a, V3 b, V3 c) {
   if (d2 < bd) { best = c2; bd = d2; }
   if (d3 < bd) { best = c3; bd = d3; }
   return best;
+}
+
+// Closest point on rectangle a, b, c, d (vertices in order, right angles):
+// the projection onto its plane if that lies inside, else the nearest point of
+// the four edges.
+V3 closest_on_rectangle(V3 p, V3 a, V3 b, V3 c, V3 d) {
+  V3 u = b - a, w = d - a;
+  V3 nrm = cross(u, w);
+  double n2 = dot(nrm, nrm);
+  if (n2 > 0.0) {
+    V3 y = p - (dot(p - a, nrm) / n2) * nrm;
+    double s = dot(y - a, u), t = dot(y - a, w);
+    if (s >= 0.0 && s <= dot(u, u) && t >= 0.0 && t <= dot(w, w)) return y;
+  }
+  V3 e[4] = {closest_on_segment(p, a, b), closest_on_segment(p, b, c),
+             closest_on_segment(p, c, d), closest_on_segment(p, d, a)};
+  V3 best = e[0];
+  double bd = dot(p - e[0], p - e[0]);
+  for (int k = 1; k < 4; ++k) {
+    double dk = dot(p - e[k], p - e[k]);
+    if (dk < bd) { best = e[k]; bd = dk; }
+  }
+  return best;
+}
+
+// Closest point of mesh element k (1 to 4 vertices: point, segment, triangle,
+// rectangle) to p, with the element's vertices given at the current pose.
+V3 closest_on_element(V3 p, const std::vector<V3>& vt, const int32_t* el) {
+  int nvk = 0;
+  while (nvk < 4 && el[nvk] >= 0) ++nvk;
+  switch (nvk) {
+    case 1: return vt[el[0]];
+    case 2: return closest_on_segment(p, vt[el[0]], vt[el[1]]);
+    case 3: return closest_on_triangle(p, vt[el[0]], vt[el[1]], vt[el[2]]);
+    default: return closest_on_rectangle(p, vt[el[0]], vt[el[1]], vt[el[2]], vt[el[3]]);
+  }
 }
 
 // Rodrigues rotation of vector r by angle th about unit axis k.
@@ -390,8 +428,7 @@ void step_once(Scene& S) {
       const V3 xi = load3(S.x.data(), i), vi = load3(S.v.data(), i), wi = load3(S.w.data(), i);
       const double Ri = S.R[i], mi = mass_of(p, Ri);
       for (int64_t k = 0; k < S.nt; ++k) {
-        const V3 pc = closest_on_triangle(xi, vt[S.tri[3 * k]], vt[S.tri[3 * k + 1]],
-                                          vt[S.tri[3 * k + 2]]);
+        const V3 pc = closest_on_element(xi, vt, &S.tri[4 * k]);
         const V3 d = xi - pc;
         const double dist = norm(d);
         const double delta = Ri + S.tri_radius[k] - dist;
@@ -447,7 +484,7 @@ void* oracle_create(const oracle_params* p, int64_t n, const double* R, const do
   S->nt = nt;
   if (nv > 0) S->vert0.assign(vert, vert + 3 * nv);
   if (nt > 0) {
-    S->tri.assign(tri, tri + 3 * nt);
+    S->tri.assign(tri, tri + 4 * nt);
     S->tri_radius.assign(tri_radius, tri_radius + nt);
   }
   return S;
@@ -520,6 +557,17 @@ void oracle_closest_on_triangle(const double* p, const double* a, const double* 
 
 double oracle_beta(double e_n) { return beta_of(e_n); }
 
+// Closest point on a mesh element given by its vertices (nverts = 1..4), for tests.
+void oracle_closest_on_element(const double* p, const double* verts, int32_t nverts, double* out) {
+  std::vector<V3> vt;
+  int32_t el[4] = {-1, -1, -1, -1};
+  for (int32_t k = 0; k < nverts && k < 4; ++k) {
+    vt.push_back(load3(verts, k));
+    el[k] = k;
+  }
+  store3(out, 0, closest_on_element(load3(p, 0), vt, el));
+}
+
 // Contact coefficients for tests: out = {E*, G*, R*, m*, k_n, k_s, c_n, c_s}.
 // For a wall (wall != 0) Rj is ignored.
 void oracle_contact_coeffs(const oracle_params* p, int32_t wall, double Ri, double Rj,
@@ -552,7 +600,7 @@ void oracle_sample_first_step(const oracle_params* p, int64_t n, const double* R
   S.step_count = step_index;
   if (nv > 0) S.vert0.assign(vert, vert + 3 * nv);
   if (nt > 0) {
-    S.tri.assign(tri, tri + 3 * nt);
+    S.tri.assign(tri, tri + 4 * nt);
     S.tri_radius.assign(tri_radius, tri_radius + nt);
   }
   std::vector<V3> vt(nv);
@@ -586,7 +634,7 @@ void oracle_sample_first_step(const oracle_params* p, int64_t n, const double* R
       }
     }
     for (int64_t k = 0; k < nt; ++k) {
-      const V3 pc = closest_on_triangle(xi, vt[tri[3 * k]], vt[tri[3 * k + 1]], vt[tri[3 * k + 2]]);
+      const V3 pc = closest_on_element(xi, vt, &S.tri[4 * k]);
       const V3 d = xi - pc;
       const double dist = norm(d);
       const double delta = Ri + tri_radius[k] - dist;

@@ -77,6 +77,7 @@ def _load():
     lib.oracle_set_contacts.argtypes = [_P, _I64, ctypes.POINTER(_I64), dp]
     lib.oracle_set_step_count.argtypes = [_P, _I64]
     lib.oracle_closest_on_triangle.argtypes = [dp, dp, dp, dp, dp]
+    lib.oracle_closest_on_element.argtypes = [dp, dp, ctypes.c_int32, dp]
     lib.oracle_beta.restype = _D
     lib.oracle_beta.argtypes = [_D]
     lib.oracle_contact_coeffs.argtypes = [ctypes.POINTER(OracleParams), ctypes.c_int32, _D, _D,
@@ -95,6 +96,20 @@ def _dptr(a: np.ndarray):
 
 def _f64(a, shape):
     return np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(shape))
+
+
+def elements(tris) -> np.ndarray:
+    """Mesh elements as an (m, 4) int32 array of vertex indices padded with -1.
+
+    Rows with 1, 2, 3 or 4 vertices are a point, a segment, a triangle or a
+    rectangle (vertices in order around it).  (m, 3) triangle arrays are padded.
+    """
+    t = np.asarray(tris)
+    if t.ndim == 1:
+        t = t.reshape(-1, 3)
+    out = np.full((t.shape[0], 4), -1, dtype=np.int32)
+    out[:, :t.shape[1]] = t
+    return np.ascontiguousarray(out)
 
 
 def make_params(p: dict, literal_sign: bool = False) -> OracleParams:
@@ -129,12 +144,12 @@ class OracleScene:
         if tris is None or len(tris) == 0:
             nv, nt = 0, 0
             vb = np.zeros(3)
-            tb = np.zeros(3, dtype=np.int32)
+            tb = np.full(4, -1, dtype=np.int32)
             rb = np.zeros(1)
         else:
             vb = _f64(verts, (-1, 3))
-            tb = np.ascontiguousarray(np.asarray(tris, dtype=np.int32).reshape(-1, 3))
-            rb = _f64(tri_radius, (-1,))
+            tb = elements(tris)
+            rb = _f64(np.zeros(len(tb)) if tri_radius is None else tri_radius, (-1,))
             nv, nt = vb.shape[0], tb.shape[0]
         self.n_tri = nt
         self._h = lib.oracle_create(ctypes.byref(self._p), n, _dptr(R), _dptr(x), _dptr(v),
@@ -204,6 +219,16 @@ def closest_on_triangle(p, a, b, c) -> np.ndarray:
     return out
 
 
+def closest_on_element(p, verts) -> np.ndarray:
+    """Closest point on a point / segment / triangle / rectangle (1-4 vertices)."""
+    lib = _load()
+    p = _f64(p, (3,))
+    v = _f64(verts, (-1, 3))
+    out = np.empty(3)
+    lib.oracle_closest_on_element(_dptr(p), _dptr(v), v.shape[0], _dptr(out))
+    return out
+
+
 def beta(e_n: float) -> float:
     return float(_load().oracle_beta(float(e_n)))
 
@@ -233,11 +258,11 @@ def sample_first_step(params: dict, R, x, v, w, q, verts, tris, tri_radius, ids,
     ids = np.ascontiguousarray(np.asarray(ids, dtype=np.int64))
     ns = ids.shape[0]
     if tris is None or len(tris) == 0:
-        vb, tb, rb, nv, nt = np.zeros(3), np.zeros(3, dtype=np.int32), np.zeros(1), 0, 0
+        vb, tb, rb, nv, nt = np.zeros(3), np.full(4, -1, dtype=np.int32), np.zeros(1), 0, 0
     else:
         vb = _f64(verts, (-1, 3))
-        tb = np.ascontiguousarray(np.asarray(tris, dtype=np.int32).reshape(-1, 3))
-        rb = _f64(tri_radius, (-1,))
+        tb = elements(tris)
+        rb = _f64(np.zeros(len(tb)) if tri_radius is None else tri_radius, (-1,))
         nv, nt = vb.shape[0], tb.shape[0]
     p = make_params(params, literal_sign)
     out = {k: np.empty((ns, 3)) for k in ("F", "T", "x", "v", "w")}
