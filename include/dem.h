@@ -1,15 +1,16 @@
 /*
  * dem.h -- C ABI of the GB300 soft-sphere DEM timestep library (libdem.so).
  *
- * The library advances a 3D ensemble of frictional spheres and a rigid
- * triangle mesh with the method of arXiv 2507.12610 ("TinyDEM"):
+ * The library advances a 3D ensemble of frictional spheres and a rigid mesh
+ * (triangles, rectangles, segments, points) with the method of arXiv
+ * 2507.12610 ("TinyDEM"):
  *   - damped Newton-Euler equations of motion with Stokes drag (Sec. 2.1,
  *     Eqs. translation / rotation),
  *   - the visco-elastic Hertz-Mindlin contact law with Coulomb-limited
  *     sliding, rolling and twisting springs whose history persists for the
  *     life of a contact (Sec. 2.2, Eqs. fn, fs, fr, ft, Coulombs/r/t; Sec. 2.3,
  *     Eqs. um, um_static, fm_kinetic, um_kinetic),
- *   - sphere-triangle mesh contacts with the wall limits R_j = E_j = m_j = inf
+ *   - sphere-mesh element contacts with the wall limits R_j = E_j = m_j = inf
  *     (Sec. 2.2) and one independent contact per touching element (Sec. 3.3),
  *   - semi-implicit Euler integration with the synchronous SPIRAL quaternion
  *     update (Sec. 2.3, Eqs. v, x, w, spiral).
@@ -78,7 +79,7 @@ typedef struct dem_params {
   double domain_hi[3];   /*   bounding box of particles and mesh, padded     */
   int32_t precision;     /* DEM_FP64 or DEM_MIXED */
   int32_t max_neighbors; /* list capacity per particle; <= 0 selects 64 */
-  int32_t max_mesh_contacts; /* triangle-candidate capacity per particle; <= 0: 16 */
+  int32_t max_mesh_contacts; /* mesh-element candidate capacity per particle; <= 0: 16 */
   int32_t record_forces; /* nonzero: keep per-particle contact sums for dem_read_forces */
 } dem_params;
 
@@ -92,22 +93,37 @@ typedef struct dem_particles {
   const double* q;   /* [n][4] unit quaternions (scalar first); NULL = identity */
 } dem_particles;
 
-/* Rigid triangle mesh in its reference pose (host arrays); may be empty. */
+/* Rigid mesh in its reference pose (host arrays); may be empty.  Its elements
+ * (Sec. 2.2, 3.3) are the triangles of `tri` followed by the rows of `elem`,
+ * numbered 0 .. n_tri + n_elem - 1 in that order; a contact with element k has
+ * the key j = -1 - k.  Each element has a radius R_j >= 0: the wall is the set
+ * of points within R_j of the element (a sphere, a capsule, a rounded plate).
+ * Rows of `elem` hold 1 to 4 vertex indices followed by -1 pads:
+ *   1 vertex   a point,
+ *   2 vertices a segment a-b,
+ *   3 vertices a triangle a-b-c,
+ *   4 vertices a rectangle a-b-c-d in order around it; its corners must be
+ *              right angles (|ab . ad| <= 1e-9 |ab| |ad|, |a + c - b - d| <=
+ *              1e-9 (|ab| + |ad|)) and its edges of nonzero length, else
+ *              dem_scene_create returns DEM_ERR_INVALID. */
 typedef struct dem_mesh {
   int64_t n_vert;
   const double* vert;        /* [n_vert][3] */
   int64_t n_tri;
   const int32_t* tri;        /* [n_tri][3] vertex indices in [0, n_vert) */
   const double* tri_radius;  /* [n_tri] element radius R_j >= 0 (Sec. 3.3); NULL = 0 */
+  int64_t n_elem;            /* further elements, numbered after the triangles */
+  const int32_t* elem;       /* [n_elem][4] vertex indices in [0, n_vert), -1 pads */
+  const double* elem_radius; /* [n_elem] element radius R_j >= 0; NULL = 0 */
 } dem_mesh;
 
 typedef struct dem_stats {
   int64_t steps;          /* steps completed */
   int64_t rebuilds;       /* neighbour-list rebuilds performed */
   int64_t pair_contacts;  /* touching particle pairs in the last step */
-  int64_t mesh_contacts;  /* touching particle-triangle pairs in the last step */
+  int64_t mesh_contacts;  /* touching particle-element pairs in the last step */
   int64_t list_entries;   /* directed candidate entries in the current list */
-  int64_t mesh_candidates;/* particle-triangle candidates in the current list */
+  int64_t mesh_candidates;/* particle-element candidates in the current list */
   int32_t max_list_len;   /* longest per-particle candidate list */
   int32_t status;         /* sticky device status (DEM_OK if none) */
   int32_t launches_per_step;    /* kernels launched in a step without a list rebuild */
@@ -119,7 +135,7 @@ typedef struct dem_scene dem_scene;
 /* Create a scene on the current CUDA device.  `stream` is a cudaStream_t (NULL:
  * the library creates its own).  Copies the host arrays to the device.
  * Errors: DEM_ERR_INVALID (parameters outside Table 2's requirements, n < 1,
- * non-finite input, bad triangle index), DEM_ERR_NOMEM, DEM_ERR_CUDA. */
+ * non-finite input, bad element), DEM_ERR_NOMEM, DEM_ERR_CUDA. */
 int dem_scene_create(const dem_params* params, const dem_particles* particles,
                      const dem_mesh* mesh, void* stream, dem_scene** out);
 
@@ -150,8 +166,8 @@ int dem_read_state(dem_scene* s, double* x, double* v, double* w, double* q);
 int dem_read_forces(dem_scene* s, double* F, double* T);
 
 /* Active contacts of the last step with their friction history.  keys[2k] = i,
- * keys[2k+1] = j in caller indices: a particle pair has i < j; a triangle
- * contact has j = -1 - triangle index.  hist[7k..7k+6] = u_s (3), u_r (3), u_t.
+ * keys[2k+1] = j in caller indices: a particle pair has i < j; a mesh
+ * contact has j = -1 - element index (see dem_mesh).  hist[7k..7k+6] = u_s (3), u_r (3), u_t.
  * Rows are sorted by (i, j).  If `capacity` is too small only the count is
  * written and DEM_ERR_CAPACITY is returned.  Synchronizes. */
 int dem_read_contacts(dem_scene* s, int64_t capacity, int64_t* keys, double* hist,

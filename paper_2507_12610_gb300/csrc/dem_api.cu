@@ -45,6 +45,76 @@ bool finite_all(const double* a, int64_t n) {
   return true;
 }
 
+// The mesh's elements as one table (Sec. 3.3): the triangles, then the rows of
+// `elem`; four vertex indices each, -1 for unused slots.
+struct ElemTable {
+  std::vector<int4> el;
+  std::vector<double> rad;
+  static int count(const int4& e) {
+    return e.w >= 0 ? 4 : (e.z >= 0 ? 3 : (e.y >= 0 ? 2 : 1));
+  }
+  static int vert(const int4& e, int j) {
+    return j == 0 ? e.x : (j == 1 ? e.y : (j == 2 ? e.z : e.w));
+  }
+};
+
+// Rectangle a-b-c-d with right angles, to the tolerance stated in dem.h.
+bool is_rectangle(const double* V, const int4& e) {
+  double u[3], w[3], gap[3], uu = 0, ww = 0, uw = 0, gg = 0;
+  for (int a = 0; a < 3; ++a) {
+    u[a] = V[3 * e.y + a] - V[3 * e.x + a];
+    w[a] = V[3 * e.w + a] - V[3 * e.x + a];
+    gap[a] = V[3 * e.x + a] + V[3 * e.z + a] - V[3 * e.y + a] - V[3 * e.w + a];
+    uu += u[a] * u[a];
+    ww += w[a] * w[a];
+    uw += u[a] * w[a];
+    gg += gap[a] * gap[a];
+  }
+  if (!(uu > 0) || !(ww > 0)) return false;
+  const double lu = std::sqrt(uu), lw = std::sqrt(ww);
+  return std::fabs(uw) <= 1e-9 * lu * lw && std::sqrt(gg) <= 1e-9 * (lu + lw);
+}
+
+// Build and check the element table; DEM_ERR_INVALID on a bad element.
+int gather_elements(const dem_mesh* me, ElemTable& t) {
+  t.el.clear();
+  t.rad.clear();
+  if (!me) return DEM_OK;
+  if (me->n_tri < 0 || me->n_elem < 0 || me->n_tri + me->n_elem > 0x7fffffff)
+    return DEM_ERR_INVALID;
+  const int64_t total = me->n_tri + me->n_elem;
+  if (total == 0) return DEM_OK;
+  if (!me->vert || me->n_vert < 1 || me->n_vert > 0x7fffffff) return DEM_ERR_INVALID;
+  if (me->n_tri > 0 && !me->tri) return DEM_ERR_INVALID;
+  if (me->n_elem > 0 && !me->elem) return DEM_ERR_INVALID;
+  if (!finite_all(me->vert, 3 * me->n_vert)) return DEM_ERR_INVALID;
+  t.el.resize(total);
+  t.rad.resize(total);
+  for (int64_t k = 0; k < me->n_tri; ++k) {
+    t.el[k] = make_int4(me->tri[3 * k], me->tri[3 * k + 1], me->tri[3 * k + 2], -1);
+    t.rad[k] = me->tri_radius ? me->tri_radius[k] : 0.0;
+    if (t.el[k].x < 0 || t.el[k].y < 0 || t.el[k].z < 0) return DEM_ERR_INVALID;
+  }
+  for (int64_t k = 0; k < me->n_elem; ++k) {
+    const int32_t* r = me->elem + 4 * k;
+    int nvk = 0;
+    while (nvk < 4 && r[nvk] >= 0) ++nvk;
+    if (nvk == 0) return DEM_ERR_INVALID;
+    for (int j = nvk; j < 4; ++j)
+      if (r[j] != -1) return DEM_ERR_INVALID;
+    t.el[me->n_tri + k] = make_int4(r[0], r[1], r[2], r[3]);
+    t.rad[me->n_tri + k] = me->elem_radius ? me->elem_radius[k] : 0.0;
+  }
+  for (int64_t k = 0; k < total; ++k) {
+    const int4& e = t.el[k];
+    for (int j = 0; j < ElemTable::count(e); ++j)
+      if (ElemTable::vert(e, j) >= me->n_vert) return DEM_ERR_INVALID;
+    if (ElemTable::count(e) == 4 && !is_rectangle(me->vert, e)) return DEM_ERR_INVALID;
+    if (!(t.rad[k] >= 0) || !std::isfinite(t.rad[k])) return DEM_ERR_INVALID;
+  }
+  return DEM_OK;
+}
+
 }  // namespace
 
 struct dem_scene {
@@ -106,15 +176,6 @@ int validate(const dem_params* pr, const dem_particles* pa, const dem_mesh* me) 
   if (pa->v && !finite_all(pa->v, 3 * n)) return DEM_ERR_INVALID;
   if (pa->w && !finite_all(pa->w, 3 * n)) return DEM_ERR_INVALID;
   if (pa->q && !finite_all(pa->q, 4 * n)) return DEM_ERR_INVALID;
-  if (me && me->n_tri > 0) {
-    if (!me->vert || !me->tri || me->n_vert < 1 || me->n_tri > 0x7fffffff) return DEM_ERR_INVALID;
-    if (!finite_all(me->vert, 3 * me->n_vert)) return DEM_ERR_INVALID;
-    for (int64_t k = 0; k < 3 * me->n_tri; ++k)
-      if (me->tri[k] < 0 || me->tri[k] >= me->n_vert) return DEM_ERR_INVALID;
-    if (me->tri_radius)
-      for (int64_t k = 0; k < me->n_tri; ++k)
-        if (!(me->tri_radius[k] >= 0) || !std::isfinite(me->tri_radius[k])) return DEM_ERR_INVALID;
-  }
   return DEM_OK;
 }
 
@@ -494,6 +555,9 @@ int dem_scene_create(const dem_params* params, const dem_particles* parts, const
   *out = nullptr;
   int rc = validate(params, parts, mesh);
   if (rc != DEM_OK) return rc;
+  ElemTable et;
+  rc = gather_elements(mesh, et);
+  if (rc != DEM_OK) return rc;
   dem_scene* s = new (std::nothrow) dem_scene();
   if (!s) return DEM_ERR_NOMEM;
   auto fail = [&](int code) {
@@ -515,8 +579,8 @@ int dem_scene_create(const dem_params* params, const dem_particles* parts, const
   s->user = *params;
   const int64_t n = parts->n;
   s->n = n;
-  const bool has_mesh = mesh && mesh->n_tri > 0;
-  s->nt = has_mesh ? (int32_t)mesh->n_tri : 0;
+  const bool has_mesh = !et.el.empty();
+  s->nt = (int32_t)et.el.size();
   s->nv = has_mesh ? (int32_t)mesh->n_vert : 0;
   Params& p = s->p;
   p.E = params->E;
@@ -589,8 +653,7 @@ int dem_scene_create(const dem_params* params, const dem_particles* parts, const
     double mrad = 0;
     if (has_mesh) {
       double rtri = 0;
-      if (mesh->tri_radius)
-        for (int64_t k = 0; k < mesh->n_tri; ++k) rtri = std::max(rtri, mesh->tri_radius[k]);
+      for (double r : et.rad) rtri = std::max(rtri, r);
       for (int64_t k = 0; k < mesh->n_vert; ++k)
         for (int a = 0; a < 3; ++a) {
           lo[a] = std::min(lo[a], mesh->vert[3 * k + a] - rtri);
@@ -714,25 +777,26 @@ int dem_scene_create(const dem_params* params, const dem_particles* parts, const
     s->bb.tcell_count = M.get<uint32_t>(ncells);
     s->bb.tcell_start = M.get<uint32_t>(ncells + 1);
     s->bb.tcell_overflow = M.get<uint32_t>(1);
-    // capacity: for every triangle, the cells of a cube around its bounding
+    // capacity: for every element, the cells of a cube around its bounding
     // ball grown by the reach (valid for any pose of a rigid mesh)
     const double reach = rmax + skin + 2.0 * p.list_margin;
     double tcap = 0;
-    for (int64_t k = 0; k < mesh->n_tri; ++k) {
+    for (int k = 0; k < s->nt; ++k) {
+      const int4 e = et.el[k];
+      const int nvk = ElemTable::count(e);
       double c[3] = {0, 0, 0};
-      for (int j = 0; j < 3; ++j)
-        for (int a = 0; a < 3; ++a) c[a] += mesh->vert[3 * mesh->tri[3 * k + j] + a] / 3.0;
+      for (int j = 0; j < nvk; ++j)
+        for (int a = 0; a < 3; ++a) c[a] += mesh->vert[3 * ElemTable::vert(e, j) + a] / nvk;
       double rb = 0;
-      for (int j = 0; j < 3; ++j) {
+      for (int j = 0; j < nvk; ++j) {
         double d2 = 0;
         for (int a = 0; a < 3; ++a) {
-          const double d = mesh->vert[3 * mesh->tri[3 * k + j] + a] - c[a];
+          const double d = mesh->vert[3 * ElemTable::vert(e, j) + a] - c[a];
           d2 += d * d;
         }
         rb = std::max(rb, std::sqrt(d2));
       }
-      const double rk = mesh->tri_radius ? mesh->tri_radius[k] : 0.0;
-      const double side = std::ceil(2.0 * (rb + rk + reach) / h) + 2.0;
+      const double side = std::ceil(2.0 * (rb + et.rad[k] + reach) / h) + 2.0;
       tcap += std::min((double)ncells, side * side * side);
     }
     if (tcap > 2.0e9) return fail(DEM_ERR_NOMEM);
@@ -741,8 +805,8 @@ int dem_scene_create(const dem_params* params, const dem_particles* parts, const
     s->mesh.ref = M.get<D4>(s->nv);
     s->mesh.tri = M.get<int4>(s->nt);
     s->mesh.rad = M.get<double>(s->nt);
-    s->mesh.cur = M.get<D4>(3 * (size_t)s->nt);
-    s->mesh.curf = M.get<float4>(3 * (size_t)s->nt);
+    s->mesh.cur = M.get<D4>(4 * (size_t)s->nt);
+    s->mesh.curf = M.get<float4>(4 * (size_t)s->nt);
   }
   if (M.failed) return fail(DEM_ERR_NOMEM);
   s->mesh.nv = s->nv;
@@ -752,15 +816,9 @@ int dem_scene_create(const dem_params* params, const dem_particles* parts, const
     std::vector<D4> ref(s->nv);
     for (int k = 0; k < s->nv; ++k)
       ref[k] = make_D4(mesh->vert[3 * k], mesh->vert[3 * k + 1], mesh->vert[3 * k + 2], 0);
-    std::vector<int4> tri(s->nt);
-    std::vector<double> rad(s->nt);
-    for (int k = 0; k < s->nt; ++k) {
-      tri[k] = make_int4(mesh->tri[3 * k], mesh->tri[3 * k + 1], mesh->tri[3 * k + 2], 0);
-      rad[k] = mesh->tri_radius ? mesh->tri_radius[k] : 0.0;
-    }
     if (cudaMemcpy(s->mesh.ref, ref.data(), s->nv * sizeof(D4), cudaMemcpyHostToDevice) ||
-        cudaMemcpy(s->mesh.tri, tri.data(), s->nt * sizeof(int4), cudaMemcpyHostToDevice) ||
-        cudaMemcpy(s->mesh.rad, rad.data(), s->nt * sizeof(double), cudaMemcpyHostToDevice))
+        cudaMemcpy(s->mesh.tri, et.el.data(), s->nt * sizeof(int4), cudaMemcpyHostToDevice) ||
+        cudaMemcpy(s->mesh.rad, et.rad.data(), s->nt * sizeof(double), cudaMemcpyHostToDevice))
       return fail(DEM_ERR_CUDA);
   }
   // kernels per step: mesh pose, [decide], rebuild (prep, clear, count, 3 scan,
@@ -943,7 +1001,7 @@ int dem_get_stats(dem_scene* s, dem_stats* out) {
 }
 
 // Save format (little-endian, native struct layout):
-//   u64 magic, u64 version, i64 n, i64 n_tri, dem_params, i64 step,
+//   u64 magic, u64 version, i64 n, i64 mesh elements, dem_params, i64 step,
 //   n records P, V, W, Q in caller order (D4 or F8 by precision),
 //   n radii (double), i64 m, m x (i64 i, i64 j, double h[7]).
 static const uint64_t kMagic = 0x4d45445f42503347ull;  // "G3PB_DEM"

@@ -58,4 +58,38 @@ __device__ __forceinline__ V3<T> closest_point_triangle(V3<T> q, V3<T> a, V3<T> 
   return a + v * ab + w * ac;
 }
 
+// Closest point on segment ab to q.
+template <typename T>
+__device__ __forceinline__ V3<T> closest_point_segment(V3<T> q, V3<T> a, V3<T> b) {
+  const V3<T> ab = b - a;
+  const T l2 = dot(ab, ab);
+  if (!(l2 > T(0))) return a;
+  T t = dot(q - a, ab) / l2;
+  t = t < T(0) ? T(0) : (t > T(1) ? T(1) : t);
+  return a + t * ab;
+}
+
+// Closest point on the rectangle with corner a and perpendicular edges a->b,
+// a->d: clamp the two edge coordinates of q (exact for right angles).
+template <typename T>
+__device__ __forceinline__ V3<T> closest_point_rectangle(V3<T> q, V3<T> a, V3<T> b, V3<T> d) {
+  const V3<T> u = b - a, w = d - a, aq = q - a;
+  T s = dot(aq, u) / dot(u, u);
+  T t = dot(aq, w) / dot(w, w);
+  s = s < T(0) ? T(0) : (s > T(1) ? T(1) : s);
+  t = t < T(0) ? T(0) : (t > T(1) ? T(1) : t);
+  return a + s * u + t * w;
+}
+
+// Closest point on a mesh element of nv vertices (Sec. 3.3): 1 point,
+// 2 segment, 3 triangle, 4 rectangle (vertices a, b, c, d in order).
+template <typename T>
+__device__ __forceinline__ V3<T> closest_point_element(V3<T> q, V3<T> a, V3<T> b, V3<T> c,
+                                                       V3<T> d, int nv) {
+  if (nv == 3) return closest_point_triangle(q, a, b, c);
+  if (nv == 4) return closest_point_rectangle(q, a, b, d);
+  if (nv == 2) return closest_point_segment(q, a, b);
+  return a;
+}
+
 }  // namespace dem

@@ -128,12 +128,14 @@ struct ListBuf {
 };
 
 // Mesh at the current pose.
+// Mesh elements (Sec. 3.3): triangles first, then points, segments and
+// rectangles; four vertex slots per element, unused slots repeat vertex 0.
 struct MeshDev {
-  D4* ref;      // [nv] reference vertices (x, y, z, 0)
-  int4* tri;         // [nt] vertex indices, w unused
+  D4* ref;           // [nv] reference vertices (x, y, z, 0)
+  int4* tri;         // [nt] vertex indices, -1 for unused slots
   double* rad;       // [nt] element radius
-  D4* cur;      // [nt][3] current triangle vertices (absolute), w of the first = radius
-  float4* curf;      // [nt][3] current vertices in shifted coordinates (float)
+  D4* cur;           // [nt][4] current vertices (absolute); .w of slot 0 = radius
+  float4* curf;      // [nt][4] current vertices, shifted (float); .w of slot 0 = vertex count
   int32_t nv, nt;
 };
 

@@ -132,21 +132,25 @@ __global__ void k_tri_cells(const Ctl* ctl, Params p, MeshDev mesh, BinBuf bb, i
   if (!rebuilding(ctl)) return;
   const int k = blockIdx.x;
   if (k >= mesh.nt) return;
-  const float4 A = mesh.curf[3 * k], B = mesh.curf[3 * k + 1], C = mesh.curf[3 * k + 2];
+  const float4 A = mesh.curf[4 * k], B = mesh.curf[4 * k + 1], C = mesh.curf[4 * k + 2],
+               D = mesh.curf[4 * k + 3];
+  const int nvk = (int)A.w;
   const float reach = (float)mesh.rad[k] + p.rmax + p.skin + p.list_margin;
-  const float3 lo = make_float3(fminf(A.x, fminf(B.x, C.x)) - reach,
-                                fminf(A.y, fminf(B.y, C.y)) - reach,
-                                fminf(A.z, fminf(B.z, C.z)) - reach);
-  const float3 hi = make_float3(fmaxf(A.x, fmaxf(B.x, C.x)) + reach,
-                                fmaxf(A.y, fmaxf(B.y, C.y)) + reach,
-                                fmaxf(A.z, fmaxf(B.z, C.z)) + reach);
+  // unused vertex slots repeat vertex 0, so the box of all four is the element's
+  const float3 lo = make_float3(fminf(fminf(A.x, B.x), fminf(C.x, D.x)) - reach,
+                                fminf(fminf(A.y, B.y), fminf(C.y, D.y)) - reach,
+                                fminf(fminf(A.z, B.z), fminf(C.z, D.z)) - reach);
+  const float3 hi = make_float3(fmaxf(fmaxf(A.x, B.x), fmaxf(C.x, D.x)) + reach,
+                                fmaxf(fmaxf(A.y, B.y), fmaxf(C.y, D.y)) + reach,
+                                fmaxf(fmaxf(A.z, B.z), fmaxf(C.z, D.z)) + reach);
   const int3 c0 = cell_coords(p, lo.x, lo.y, lo.z);
   const int3 c1 = cell_coords(p, hi.x, hi.y, hi.z);
   const int nx = c1.x - c0.x + 1, ny = c1.y - c0.y + 1, nz = c1.z - c0.z + 1;
   const int64_t total = (int64_t)nx * ny * nz;
   const float halfdiag = 0.5f * p.h * 1.7320508f * 1.0001f;
   const float lim = reach + halfdiag;
-  const V3<float> a = mk(A.x, A.y, A.z), b = mk(B.x, B.y, B.z), c = mk(C.x, C.y, C.z);
+  const V3<float> a = mk(A.x, A.y, A.z), b = mk(B.x, B.y, B.z), c = mk(C.x, C.y, C.z),
+                  dd = mk(D.x, D.y, D.z);
   for (int64_t i = threadIdx.x; i < total; i += blockDim.x) {
     const int cx = c0.x + (int)(i % nx);
     const int cy = c0.y + (int)((i / nx) % ny);
@@ -160,7 +164,7 @@ __global__ void k_tri_cells(const Ctl* ctl, Params p, MeshDev mesh, BinBuf bb, i
                       cy == p.nc[1] - 1 || cz == p.nc[2] - 1;
     bool hit = edge;
     if (!hit) {
-      const V3<float> y = closest_point_triangle(q, a, b, c);
+      const V3<float> y = closest_point_element(q, a, b, c, dd, nvk);
       const V3<float> d = q - y;
       hit = dot(d, d) <= lim * lim;
     }
@@ -292,9 +296,10 @@ k_list_build(Ctl* ctl, Params p, BinBuf bb, Lists L, MeshDev mesh) {
     bool tover = false;
     for (uint32_t i = a; i < b; ++i) {
       const uint32_t k = bb.tcell_tri[i];
-      const float4 A = mesh.curf[3 * k], B = mesh.curf[3 * k + 1], C = mesh.curf[3 * k + 2];
-      const V3<float> y = closest_point_triangle(q, mk(A.x, A.y, A.z), mk(B.x, B.y, B.z),
-                                                 mk(C.x, C.y, C.z));
+      const float4 A = mesh.curf[4 * k], B = mesh.curf[4 * k + 1], C = mesh.curf[4 * k + 2],
+                   D = mesh.curf[4 * k + 3];
+      const V3<float> y = closest_point_element(q, mk(A.x, A.y, A.z), mk(B.x, B.y, B.z),
+                                                mk(C.x, C.y, C.z), mk(D.x, D.y, D.z), (int)A.w);
       const V3<float> d = q - y;
       const float cut = X.w + (float)mesh.rad[k] + p.skin + p.list_margin;
       if (dot(d, d) >= cut * cut) continue;

@@ -28,11 +28,13 @@ namespace {
 
 __global__ void k_mesh_pose(const Ctl* ctl, Params p, MeshDev mesh) {
   if (ctl->status) return;
-  const int slot = blockIdx.x * blockDim.x + threadIdx.x;  // triangle-vertex slot
-  if (slot >= 3 * mesh.nt) return;
-  const int k = slot / 3, j = slot - 3 * k;
+  const int slot = blockIdx.x * blockDim.x + threadIdx.x;  // element-vertex slot
+  if (slot >= 4 * mesh.nt) return;
+  const int k = slot >> 2, j = slot & 3;
   const int4 tv = mesh.tri[k];
-  const D4 r0 = mesh.ref[j == 0 ? tv.x : (j == 1 ? tv.y : tv.z)];
+  const int nvk = tv.w >= 0 ? 4 : (tv.z >= 0 ? 3 : (tv.y >= 0 ? 2 : 1));
+  const int vi = j == 0 ? tv.x : (j == 1 ? tv.y : (j == 2 ? tv.z : tv.w));
+  const D4 r0 = mesh.ref[j < nvk ? vi : tv.x];
   V3<double> pos = xyz(r0);
   const double wn = p.omega_norm;
   if (wn > 0.0) {
@@ -45,7 +47,7 @@ __global__ void k_mesh_pose(const Ctl* ctl, Params p, MeshDev mesh) {
   }
   mesh.cur[slot] = make_D4(pos.x, pos.y, pos.z, j == 0 ? mesh.rad[k] : 0.0);
   mesh.curf[slot] = make_float4((float)(pos.x - p.origin[0]), (float)(pos.y - p.origin[1]),
-                                (float)(pos.z - p.origin[2]), 0.f);
+                                (float)(pos.z - p.origin[2]), j == 0 ? (float)nvk : 0.f);
 }
 
 // Rotation of the mesh at the control block's step (after a host upload); the
@@ -256,14 +258,17 @@ struct MixedPolicy {
                               (Pt.hi.z - p.center_hi[2]) + (Pt.lo.z - p.center_lo[2]));
       for (int m = 0; m < ntc; ++m) {
         const uint32_t kt = lb.tric[(size_t)m * n + t];
-        const float4 Af = mesh.curf[3 * kt], Bf = mesh.curf[3 * kt + 1], Cf = mesh.curf[3 * kt + 2];
-        const V3<float> yf = closest_point_triangle(qf, hi3(Af), hi3(Bf), hi3(Cf));
+        const float4 Af = mesh.curf[4 * kt], Bf = mesh.curf[4 * kt + 1],
+                     Cf = mesh.curf[4 * kt + 2], Df = mesh.curf[4 * kt + 3];
+        const int nvk = (int)Af.w;
+        const V3<float> yf =
+            closest_point_element(qf, hi3(Af), hi3(Bf), hi3(Cf), hi3(Df), nvk);
         const V3<float> df = qf - yf;
-        const D4 A = mesh.cur[3 * kt];
+        const D4 A = mesh.cur[4 * kt];
         const float reachf = Rt + (float)A.w + p.mesh_prefilter;
         if (dot(df, df) > reachf * reachf) continue;
-        const D4 B = mesh.cur[3 * kt + 1], C = mesh.cur[3 * kt + 2];
-        const V3<double> pc = closest_point_triangle(xd, xyz(A), xyz(B), xyz(C));
+        const D4 B = mesh.cur[4 * kt + 1], C = mesh.cur[4 * kt + 2], D = mesh.cur[4 * kt + 3];
+        const V3<double> pc = closest_point_element(xd, xyz(A), xyz(B), xyz(C), xyz(D), nvk);
         const V3<double> dd = xd - pc;
         const double distd = sqrt(dot(dd, dd));
         const double deltad = ((double)Pt.hi.w + (double)Pt.lo.w) + A.w - distd;
@@ -382,7 +387,7 @@ struct MixedPolicy {
 
 void launch_mesh_pose(cudaStream_t st, const Ctl* ctl, const Params& p, MeshDev mesh) {
   if (mesh.nt <= 0) return;
-  k_mesh_pose<<<(unsigned)((3 * mesh.nt + 127) / 128), 128, 0, st>>>(ctl, p, mesh);
+  k_mesh_pose<<<(unsigned)((4 * mesh.nt + 127) / 128), 128, 0, st>>>(ctl, p, mesh);
 }
 
 void launch_step(cudaStream_t st, Ctl* ctl, const Params& p, StateBufs sb, Lists L,

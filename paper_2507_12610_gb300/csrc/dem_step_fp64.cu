@@ -127,8 +127,10 @@ struct Fp64Policy {
       const V3<double> ctr = mk(p.mesh_center[0], p.mesh_center[1], p.mesh_center[2]);
       for (int m = 0; m < ntc; ++m) {
         const uint32_t kt = lb.tric[(size_t)m * n + t];
-        const D4 A = mesh.cur[3 * kt], B = mesh.cur[3 * kt + 1], C = mesh.cur[3 * kt + 2];
-        const V3<double> pc = closest_point_triangle(x, xyz(A), xyz(B), xyz(C));
+        const D4 A = mesh.cur[4 * kt], B = mesh.cur[4 * kt + 1], C = mesh.cur[4 * kt + 2],
+                 D = mesh.cur[4 * kt + 3];
+        const int nvk = (int)mesh.curf[4 * kt].w;
+        const V3<double> pc = closest_point_element(x, xyz(A), xyz(B), xyz(C), xyz(D), nvk);
         const V3<double> d = x - pc;
         const double dist = sqrt(dot(d, d));
         const double delta = Pt.w + A.w - dist;

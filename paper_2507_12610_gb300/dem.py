@@ -54,7 +54,9 @@ class dem_particles(ctypes.Structure):
 
 class dem_mesh(ctypes.Structure):
     _fields_ = [("n_vert", _I64), ("vert", _DP), ("n_tri", _I64),
-                ("tri", ctypes.POINTER(ctypes.c_int32)), ("tri_radius", _DP)]
+                ("tri", ctypes.POINTER(ctypes.c_int32)), ("tri_radius", _DP),
+                ("n_elem", _I64), ("elem", ctypes.POINTER(ctypes.c_int32)),
+                ("elem_radius", _DP)]
 
 
 class dem_stats(ctypes.Structure):
@@ -173,7 +175,8 @@ class Scene:
     """Owner of one `dem_scene*` created from host arrays."""
 
     def __init__(self, params: dict, R, x, v=None, w=None, q=None, verts=None, tris=None,
-                 tri_radius=None, precision: int = DEM_FP64, skin: float = 0.0,
+                 tri_radius=None, elems=None, elem_radius=None,
+                 precision: int = DEM_FP64, skin: float = 0.0,
                  max_neighbors: int = 0, max_mesh_contacts: int = 0,
                  record_forces: bool = False, domain=None, stream=None):
         lib = load()
@@ -192,14 +195,23 @@ class Scene:
         pa = dem_particles(n, _p(R), _p(x), _p(v), _p(w), _p(q))
         keep = [R, x, v, w, q]
         me = dem_mesh()
-        if tris is not None and len(tris):
+        has_tris = tris is not None and len(tris) > 0
+        has_elems = elems is not None and len(elems) > 0
+        if has_tris or has_elems:
+            # elements: the triangles, then the rows of `elems` (1-4 vertex
+            # indices padded with -1: point, segment, triangle, rectangle)
+            i32p = ctypes.POINTER(ctypes.c_int32)
             V = _f64(verts, (-1, 3))
-            T = np.ascontiguousarray(np.asarray(tris, dtype=np.int32).reshape(-1, 3))
+            T = np.ascontiguousarray(np.asarray(tris if has_tris else np.zeros((0, 3)),
+                                                dtype=np.int32).reshape(-1, 3))
             Rt = None if tri_radius is None else _f64(tri_radius, (-1,))
-            me = dem_mesh(V.shape[0], _p(V), T.shape[0],
-                          T.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _p(Rt))
-            keep += [V, T, Rt]
-        self.n_tri = me.n_tri
+            El = np.ascontiguousarray(np.asarray(elems if has_elems else np.zeros((0, 4)),
+                                                 dtype=np.int32).reshape(-1, 4))
+            Re = None if elem_radius is None else _f64(elem_radius, (-1,))
+            me = dem_mesh(V.shape[0], _p(V), T.shape[0], T.ctypes.data_as(i32p), _p(Rt),
+                          El.shape[0], El.ctypes.data_as(i32p), _p(Re))
+            keep += [V, T, Rt, El, Re]
+        self.n_tri = me.n_tri + me.n_elem  # mesh elements (triangles first)
         st = stream if stream is not None else current_stream()
         rc = lib.dem_scene_create(ctypes.byref(self._pp), ctypes.byref(pa), ctypes.byref(me), st,
                                   ctypes.byref(self._h))
@@ -209,7 +221,8 @@ class Scene:
     @classmethod
     def from_dict(cls, s: dict, **kw):
         return cls(s["params"], s["R"], s["x"], s.get("v"), s.get("w"), s.get("q"),
-                   s.get("verts"), s.get("tris"), s.get("tri_radius"), **kw)
+                   s.get("verts"), s.get("tris"), s.get("tri_radius"), s.get("elems"),
+                   s.get("elem_radius"), **kw)
 
     def close(self):
         if getattr(self, "_h", None) and self._h.value:

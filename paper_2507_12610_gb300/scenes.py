@@ -93,9 +93,27 @@ def drum_mesh(radius, length, n_theta=128, n_rings=15):
     return np.array(V, dtype=np.float64), np.array(T, dtype=np.int32)
 
 
-def _scene(name, seed, params, R, x, v, w, q, V, T, tri_radius, domain):
+def _scene(name, seed, params, R, x, v, w, q, V, T, tri_radius, domain, elems=None,
+           elem_radius=None):
     return dict(name=name, seed=seed, params=params, R=R, x=x, v=v, w=w, q=q, verts=V,
-                tris=T, tri_radius=tri_radius, domain=domain)
+                tris=T, tri_radius=tri_radius, elems=elems, elem_radius=elem_radius,
+                domain=domain)
+
+
+def all_elements(s):
+    """(verts, elements (m, 4) padded with -1, radii) of a scene's mesh: its
+    triangles first, then its other elements, the numbering of contact keys."""
+    T = np.asarray(s["tris"] if s.get("tris") is not None else np.zeros((0, 3)), dtype=np.int32)
+    El = np.full((T.shape[0], 4), -1, dtype=np.int32)
+    El[:, :3] = T.reshape(-1, 3)
+    rt = s.get("tri_radius")
+    rad = np.zeros(T.shape[0]) if rt is None else np.asarray(rt, dtype=np.float64)
+    if s.get("elems") is not None and len(s["elems"]):
+        El = np.vstack([El, np.asarray(s["elems"], dtype=np.int32).reshape(-1, 4)])
+        er = s.get("elem_radius")
+        rad = np.concatenate([rad, np.zeros(len(s["elems"])) if er is None
+                              else np.asarray(er, dtype=np.float64)])
+    return np.asarray(s["verts"], dtype=np.float64).reshape(-1, 3), El, rad
 
 
 def box_scene(n=1000, seed=1, speed=0.0, gravity=True, size=(0.020, 0.020, 0.060),
@@ -260,3 +278,71 @@ def drum_scene(n=1_000_000, seed=5, n_theta=128, n_rings=15, r_range=(0.8e-3, 1.
     s["drum_radius"] = radius
     s["drum_length"] = length
     return s
+
+
+def primitives_scene(n_side=(8, 8, 8), seed=6, spacing=1.96e-3, r_range=(0.9e-3, 1.1e-3),
+                     jitter=2e-5, speed=0.02, spin=0.0, omega=0.0, **over):
+    """Every kind of mesh element (Sec. 3.3) around and inside a particle lattice.
+
+    A simple cubic lattice (as in lattice_box_scene, initial overlaps) in a box
+    of six rectangles (one a rounded plate of radius 0.3 mm, set back by its
+    radius), with obstacles placed on the lattice's interstitial lines and
+    planes so that their nearest particles overlap them by at most ~0.1 mm:
+      a capsule (segment, radius 0.35 mm) along x between two rows,
+      a sphere (point, radius 0.7 mm) at the centre of a lattice cube,
+      a triangle (radius 0) in the plane between two layers,
+      a square plate (rectangle, radius 0.05 mm) across x between two columns.
+    omega turns the whole mesh about the vertical axis through the box centre.
+    Elements: 1 triangle, then 6 + 1 rectangles, 1 segment, 1 point.
+    """
+    rng = np.random.default_rng(seed)
+    nx, ny, nz = n_side
+    gi = np.stack(np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij"),
+                  axis=-1).reshape(-1, 3).astype(np.float64)
+    n = gi.shape[0]
+    R = rng.uniform(r_range[0], r_range[1], size=n)
+    c0 = np.array([-0.5 * (nx - 1) * spacing, -0.5 * (ny - 1) * spacing, r_range[1]])
+    X = gi * spacing + c0
+    if jitter > 0:
+        X += rng.uniform(-jitter, jitter, size=X.shape)
+    v = rng.normal(scale=speed, size=(n, 3)) if speed > 0 else np.zeros((n, 3))
+    w = rng.normal(scale=spin, size=(n, 3)) if spin > 0 else np.zeros((n, 3))
+    q = _unit_quaternions(rng, n)
+
+    def site(i, j, k):  # lattice coordinates -> position (half-integers allowed)
+        return c0 + spacing * np.array([i, j, k], dtype=np.float64)
+
+    lo = X.min(axis=0) - r_range[1] * 1.01
+    hi = X.max(axis=0) + r_range[1] * 1.01
+    lo[2] = 0.0
+    Vb, _ = box_mesh(lo, hi)
+    plate_r = 0.3e-3
+    Vb[[1, 2, 5, 6], 0] += plate_r  # the +x face is the rounded plate, set back
+    faces = [(0, 1, 2, 3), (4, 7, 6, 5), (0, 4, 5, 1), (1, 5, 6, 2), (2, 6, 7, 3), (3, 7, 4, 0)]
+    verts = [*Vb]
+    tri_v = [site(1.5, 1.5, 5.5), site(5.5, 2.5, 5.5), site(3.0, 5.5, 5.5)]
+    ti = len(verts)
+    verts += tri_v
+    sq = [site(4.5, 2.0, 3.6), site(4.5, 5.0, 3.6), site(4.5, 5.0, 4.9), site(4.5, 2.0, 4.9)]
+    ri = len(verts)
+    verts += sq
+    si = len(verts)
+    verts += [site(1.2, 3.5, 2.5), site(5.8, 3.5, 2.5)]
+    pi = len(verts)
+    verts += [site(1.5, 5.5, 0.5)]
+    V = np.array(verts, dtype=np.float64)
+    T = np.array([[ti, ti + 1, ti + 2]], dtype=np.int32)
+    E = [list(f) for f in faces] + [[ri, ri + 1, ri + 2, ri + 3], [si, si + 1, -1, -1],
+                                    [pi, -1, -1, -1]]
+    E = np.array(E, dtype=np.int32)
+    er = np.zeros(len(E))
+    er[3] = plate_r  # face (1, 5, 6, 2): +x
+    er[6], er[7], er[8] = 0.05e-3, 0.35e-3, 0.7e-3
+    centre = 0.5 * (lo + hi)
+    params = base_params(dt=DT_BOX, mesh_omega=(0.0, 0.0, omega),
+                         mesh_center=(centre[0], centre[1], 0.0))
+    params.update(over)
+    dlo = lo - 2 * r_range[1] - plate_r
+    dhi = hi + 2 * r_range[1] + plate_r
+    return _scene("primitives", seed, params, R, X, v, w, q, V, T, np.zeros(1), (dlo, dhi),
+                  elems=E, elem_radius=er)

@@ -52,7 +52,7 @@ def test_struct_layouts_match_header():
     from paper_2507_12610_gb300 import dem
     assert ctypes.sizeof(dem.dem_params) == 8 * (8 + 3 + 1 + 3 + 3 + 1 + 3 + 3) + 4 * 4
     assert ctypes.sizeof(dem.dem_particles) == 8 * 6
-    assert ctypes.sizeof(dem.dem_mesh) == 8 * 5
+    assert ctypes.sizeof(dem.dem_mesh) == 8 * 8
     assert ctypes.sizeof(dem.dem_stats) == 8 * 6 + 4 * 4
 
 
@@ -69,3 +69,28 @@ def test_oracle_and_library_share_no_code():
     for f in ("dem.py", "build.py", "scenes.py"):
         txt = open(os.path.join(ROOT, "paper_2507_12610_gb300", f)).read()
         assert "import oracle" not in txt and "from oracle" not in txt, f
+
+
+def test_bad_mesh_elements_are_rejected_on_the_host():
+    # element checks run before any CUDA call, so this needs no GPU: a
+    # rectangle without right angles, a pad other than -1, a vertex index out
+    # of range, an empty row and a negative radius each give DEM_ERR_INVALID
+    import numpy as np
+    from paper_2507_12610_gb300 import build, dem, scenes
+    build.build()
+    s = scenes.primitives_scene(n_side=(2, 2, 2))
+    E, er = s["elems"], s["elem_radius"]
+    V = s["verts"]
+    skew = V.copy()
+    skew[E[6, 2]] += np.array([0.0, 1e-4, 0.0])  # corner c off the plate's plane
+    cases = []
+    e = E.copy(); e[7, 3] = 0; cases.append((V, e, er))       # pad not -1
+    e = E.copy(); e[8, 0] = len(V); cases.append((V, e, er))  # index out of range
+    e = E.copy(); e[8, :] = -1; cases.append((V, e, er))      # no vertex
+    r = er.copy(); r[7] = -1e-3; cases.append((V, E, r))      # negative radius
+    cases.append((skew, E, er))                               # not a rectangle
+    for Vc, Ec, rc in cases:
+        bad = dict(s, verts=Vc, elems=Ec, elem_radius=rc)
+        with pytest.raises(dem.DemError) as err:
+            dem.Scene.from_dict(bad)
+        assert err.value.code == dem.DEM_ERR_INVALID

@@ -40,12 +40,17 @@ def rel(a, b):
     return float(np.abs(a - b).max() / den) if den > 0 else float(np.abs(a - b).max())
 
 
+def oracle_scene(oracle_mod, s):
+    V, El, rad = scenes.all_elements(s)
+    return oracle_mod.OracleScene(s["params"], s["R"], s["x"], s["v"], s["w"], s["q"], V, El,
+                                  rad)
+
+
 def run_pair(dem, oracle_mod, s, steps, precision, **kw):
     sc = dem.Scene.from_dict(s, precision=precision, record_forces=True, **kw)
     sc.step(steps)
     assert sc.synchronize() == 0
-    oc = oracle_mod.OracleScene(s["params"], s["R"], s["x"], s["v"], s["w"], s["q"], s["verts"],
-                                s["tris"], s["tri_radius"])
+    oc = oracle_scene(oracle_mod, s)
     oc.step(steps)
     return sc, oc
 
@@ -86,13 +91,16 @@ SCENES = {
     "drum_small": lambda: scenes.drum_scene(n=1500, seed=4, n_theta=32, n_rings=4,
                                             nn_dist=2.3e-3, radius=0.022),
     "column_2000": lambda: scenes.column_scene(n=2000, seed=3, spacing=2.7e-3),
+    # points, segments, triangles, rectangles (Sec. 3.3), resting and turning
+    "primitives": lambda: scenes.primitives_scene(),
+    "primitives_turning": lambda: scenes.primitives_scene(omega=20.0),
 }
 # Scenes whose contacts slide, roll and twist at their Coulomb limit for many
 # steps: there the friction update of Sec. 2.3 is discontinuous (a static step
 # adds dt v to the spring, a kinetic step does not), so a 1e-7 difference in
 # |f| versus mu |f_n| can move one spring by dt v.  DEM_MIXED is checked on
 # them by the branch-flip test below instead of the 1e-5 bound.
-MIXED_SKIP = {"lattice_spinning", "column_2000"}
+MIXED_SKIP = {"lattice_spinning", "column_2000", "primitives", "primitives_turning"}
 
 
 @pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
@@ -103,6 +111,11 @@ def test_parity_after_100_steps(dem, oracle_mod, name, precision):
     s = SCENES[name]()
     sc, oc = run_pair(dem, oracle_mod, s, 100, precision)
     compare(sc, oc, s, precision, f"{name}/{precision}")
+    if name.startswith("primitives"):
+        # the triangle, the inner plate, the capsule and the sphere all touch
+        k, _ = sc.contacts()
+        touched = set((-1 - k[k[:, 1] < 0, 1]).tolist())
+        assert {0, 7, 8, 9} <= touched, touched
 
 
 @pytest.mark.parametrize("name", sorted(MIXED_SKIP))
@@ -113,8 +126,7 @@ def test_mixed_branch_flips_are_isolated(dem, oracle_mod, name):
     # contacts whose spring jumps by about dt |v| while the others still agree.
     s = SCENES[name]()
     sc = dem.Scene.from_dict(s, precision=1, record_forces=True)
-    oc = oracle_mod.OracleScene(s["params"], s["R"], s["x"], s["v"], s["w"], s["q"],
-                                s["verts"], s["tris"], s["tri_radius"])
+    oc = oracle_scene(oracle_mod, s)
     flips_seen = False
     for step in range(1, 101):
         sc.step(1)
