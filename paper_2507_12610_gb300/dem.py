@@ -185,6 +185,7 @@ class Scene:
         R = _f64(R, (-1,))
         n = R.shape[0]
         self.n = n
+        self.R = R.copy()
         x = _f64(x, (n, 3))
         v = None if v is None else _f64(v, (n, 3))
         w = None if w is None else _f64(w, (n, 3))
