@@ -172,6 +172,29 @@ struct Lists {
   ListBuf b[2];
 };
 
+// Buffer b (0 or 1) of a double-buffered kernel parameter.  Device code must
+// use these instead of indexing the arrays with a run-time value: indexing a
+// parameter array that way makes every thread copy the whole parameter to
+// local memory first, while a select of two fields keeps it in the constant
+// bank.
+#ifdef __CUDACC__
+__device__ __forceinline__ void* buf_of(void* const (&a)[2], uint32_t b) {
+  return b ? a[1] : a[0];
+}
+__device__ __forceinline__ ListBuf list_of(const Lists& L, uint32_t b) {
+  ListBuf r;
+  r.gid = b ? L.b[1].gid : L.b[0].gid;
+  r.posf = b ? L.b[1].posf : L.b[0].posf;
+  r.meta = b ? L.b[1].meta : L.b[0].meta;
+  r.offs = b ? L.b[1].offs : L.b[0].offs;
+  r.nbr = b ? L.b[1].nbr : L.b[0].nbr;
+  r.hpp = b ? L.b[1].hpp : L.b[0].hpp;
+  r.tric = b ? L.b[1].tric : L.b[0].tric;
+  r.hpm = b ? L.b[1].hpm : L.b[0].hpm;
+  return r;
+}
+#endif
+
 // Kernel launch helpers implemented in the .cu files.
 void launch_mesh_pose(cudaStream_t st, const Ctl* ctl, const Params& p, MeshDev mesh);
 void launch_rebuild(cudaStream_t st, Ctl* ctl, const Params& p, StateBufs sb, Lists L,

@@ -58,7 +58,7 @@ k_bin_count(const Ctl* ctl, Params p, StateBufs sb, BinBuf bb) {
   if (!rebuilding(ctl)) return;
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= p.n) return;
-  const float4 X = posf_of(p, sb.P[ctl->phase & 1u], s);
+  const float4 X = posf_of(p, buf_of(sb.P, ctl->phase & 1u), s);
   const uint32_t c = cell_index(p, cell_coords(p, X.x, X.y, X.z));
   bb.key[s] = c;
   bb.local[s] = atomicAdd(&bb.cell_count[c], 1u);
@@ -77,7 +77,7 @@ k_scatter(const Ctl* ctl, Params p, BinBuf bb) {
 __global__ void __launch_bounds__(kThreads)
 k_cell_sort(const Ctl* ctl, Params p, BinBuf bb, Lists L) {
   if (!rebuilding(ctl)) return;
-  const uint32_t* gid_old = L.b[ctl->lphase & 1u].gid;
+  const uint32_t* gid_old = list_of(L, ctl->lphase & 1u).gid;
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < p.ncells;
        c += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t a = bb.cell_start[c], b = bb.cell_start[c + 1];
@@ -102,17 +102,17 @@ k_permute(const Ctl* ctl, Params p, BinBuf bb, StateBufs sb, Lists L) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= p.n) return;
   const uint32_t ph = ctl->phase & 1u, lph = ctl->lphase & 1u;
-  const Rec* P0 = static_cast<const Rec*>(sb.P[ph]);
-  const Rec* V0 = static_cast<const Rec*>(sb.V[ph]);
-  const Rec* W0 = static_cast<const Rec*>(sb.W[ph]);
-  const Rec* Q0 = static_cast<const Rec*>(sb.Q[ph]);
-  Rec* P1 = static_cast<Rec*>(sb.P[ph ^ 1u]);
-  Rec* V1 = static_cast<Rec*>(sb.V[ph ^ 1u]);
-  Rec* W1 = static_cast<Rec*>(sb.W[ph ^ 1u]);
-  Rec* Q1 = static_cast<Rec*>(sb.Q[ph ^ 1u]);
-  const uint32_t* gid_old = L.b[lph].gid;
-  uint32_t* gid_new = L.b[lph ^ 1u].gid;
-  float4* posf_new = L.b[lph ^ 1u].posf;
+  const Rec* P0 = static_cast<const Rec*>(buf_of(sb.P, ph));
+  const Rec* V0 = static_cast<const Rec*>(buf_of(sb.V, ph));
+  const Rec* W0 = static_cast<const Rec*>(buf_of(sb.W, ph));
+  const Rec* Q0 = static_cast<const Rec*>(buf_of(sb.Q, ph));
+  Rec* P1 = static_cast<Rec*>(buf_of(sb.P, ph ^ 1u));
+  Rec* V1 = static_cast<Rec*>(buf_of(sb.V, ph ^ 1u));
+  Rec* W1 = static_cast<Rec*>(buf_of(sb.W, ph ^ 1u));
+  Rec* Q1 = static_cast<Rec*>(buf_of(sb.Q, ph ^ 1u));
+  const uint32_t* gid_old = list_of(L, lph).gid;
+  uint32_t* gid_new = list_of(L, lph ^ 1u).gid;
+  float4* posf_new = list_of(L, lph ^ 1u).posf;
   const uint32_t s = bb.order[t];
   P1[t] = P0[s];
   V1[t] = V0[s];
@@ -224,8 +224,8 @@ k_list_build(Ctl* ctl, Params p, BinBuf bb, Lists L, MeshDev mesh) {
   if (!rebuilding(ctl)) return;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= p.n) return;
-  const ListBuf lo = L.b[ctl->lphase & 1u];
-  const ListBuf ln = L.b[(ctl->lphase & 1u) ^ 1u];
+  const ListBuf lo = list_of(L, ctl->lphase & 1u);
+  const ListBuf ln = list_of(L, (ctl->lphase & 1u) ^ 1u);
   const int n = p.n;
   const float4 X = ln.posf[t];
   const uint32_t gt = ln.gid[t];
@@ -338,8 +338,8 @@ k_list_compact(Ctl* ctl, Params p, BinBuf bb, Lists L) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int n = p.n;
   if (t > n) return;
-  const ListBuf lo = L.b[ctl->lphase & 1u];
-  const ListBuf ln = L.b[(ctl->lphase & 1u) ^ 1u];
+  const ListBuf lo = list_of(L, ctl->lphase & 1u);
+  const ListBuf ln = list_of(L, (ctl->lphase & 1u) ^ 1u);
   const uint32_t off = bb.tmp_offs[t];
   ln.offs[t] = off;
   if (t == n) return;

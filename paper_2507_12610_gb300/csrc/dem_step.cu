@@ -237,7 +237,7 @@ struct MixedPolicy {
                                                 bool& bad) {
     const int n = p.n;
     const int ntc = (int)ntc_u;
-    const F8* Q = static_cast<const F8*>(sb.Q[ph]);
+    const F8* Q = static_cast<const F8*>(buf_of(sb.Q, ph));
     const float Rt = Pt.hi.w + Pt.lo.w;
     Acc3& F = sums.F;
     Acc3& T = sums.T;
@@ -361,10 +361,10 @@ struct MixedPolicy {
     acc(Wn.hi.x, Wn.lo.x, dt * al.x);
     acc(Wn.hi.y, Wn.lo.y, dt * al.y);
     acc(Wn.hi.z, Wn.lo.z, dt * al.z);
-    static_cast<F8*>(sb.P[ph ^ 1u])[t] = Pn;
-    static_cast<F8*>(sb.V[ph ^ 1u])[t] = Vn;
-    static_cast<F8*>(sb.W[ph ^ 1u])[t] = Wn;
-    static_cast<F8*>(sb.Q[ph ^ 1u])[t] = Qn;
+    static_cast<F8*>(buf_of(sb.P, ph ^ 1u))[t] = Pn;
+    static_cast<F8*>(buf_of(sb.V, ph ^ 1u))[t] = Vn;
+    static_cast<F8*>(buf_of(sb.W, ph ^ 1u))[t] = Wn;
+    static_cast<F8*>(buf_of(sb.Q, ph ^ 1u))[t] = Qn;
     if (p.record_forces) {
       double* fo = forces + 6 * (size_t)t;
       fo[0] = (double)F.hx + (double)F.lx;

@@ -115,7 +115,7 @@ struct Fp64Policy {
                                                 uint32_t& nmesh, bool& disp, bool& bad) {
     const int n = p.n;
     const int ntc = (int)ntc_u;
-    const D4* Q = static_cast<const D4*>(sb.Q[ph]);
+    const D4* Q = static_cast<const D4*>(buf_of(sb.Q, ph));
     V3<double>& F = sums.F;
     V3<double>& T = sums.T;
     // particle-triangle contacts
@@ -195,10 +195,10 @@ struct Fp64Policy {
       q[0] = o4[0]; q[1] = o4[1]; q[2] = o4[2]; q[3] = o4[3];
     }
     w = w + p.dt * al;
-    D4* Pn = static_cast<D4*>(sb.P[ph ^ 1u]);
-    D4* Vn = static_cast<D4*>(sb.V[ph ^ 1u]);
-    D4* Wn = static_cast<D4*>(sb.W[ph ^ 1u]);
-    D4* Qn = static_cast<D4*>(sb.Q[ph ^ 1u]);
+    D4* Pn = static_cast<D4*>(buf_of(sb.P, ph ^ 1u));
+    D4* Vn = static_cast<D4*>(buf_of(sb.V, ph ^ 1u));
+    D4* Wn = static_cast<D4*>(buf_of(sb.W, ph ^ 1u));
+    D4* Qn = static_cast<D4*>(buf_of(sb.Q, ph ^ 1u));
     Pn[t] = make_D4(x.x, x.y, x.z, R);
     Vn[t] = make_D4(v.x, v.y, v.z, mass);
     Wn[t] = make_D4(w.x, w.y, w.z, 0.0);

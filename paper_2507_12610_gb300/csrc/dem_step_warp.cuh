@@ -69,10 +69,10 @@ k_step_warp(Ctl* ctl, Params p, StateBufs sb, Lists L, MeshDev mesh, double* for
   const uint32_t ph = ctl->phase & 1u, lph = ctl->lphase & 1u;
   const uint32_t stamp_now = (uint32_t)ctl->step;
   const uint32_t stamp_new = stamp_now + 1u;
-  const Rec* P = static_cast<const Rec*>(sb.P[ph]);
-  const Rec* V = static_cast<const Rec*>(sb.V[ph]);
-  const Rec* W = static_cast<const Rec*>(sb.W[ph]);
-  const ListBuf lb = L.b[lph];
+  const Rec* P = static_cast<const Rec*>(buf_of(sb.P, ph));
+  const Rec* V = static_cast<const Rec*>(buf_of(sb.V, ph));
+  const Rec* W = static_cast<const Rec*>(buf_of(sb.W, ph));
+  const ListBuf lb = list_of(L, lph);
   Hist* H = static_cast<Hist*>(lb.hpp);
 
   const uint32_t meta = valid ? lb.meta[t] : 0u;
