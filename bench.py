@@ -281,7 +281,8 @@ def bench_ours(a):
                       "settle_steps": a.settle, "seed": 5,
                       "rebuilds_in_timed": st["rebuilds"] - st0["rebuilds"],
                       "pair_contacts": st["pair_contacts"], "mesh_contacts": st["mesh_contacts"],
-                      "list_entries": st["list_entries"]},
+                      "list_entries": st["list_entries"],
+                      "mesh_candidates": st["mesh_candidates"]},
            "gpu_launches": int(a.steps * st["launches_per_step"]
                                + (st["rebuilds"] - st0["rebuilds"]) * st["launches_per_rebuild"]),
            "roofline": roofline}

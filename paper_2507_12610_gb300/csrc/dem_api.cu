@@ -807,6 +807,8 @@ int dem_scene_create(const dem_params* params, const dem_particles* parts, const
     s->mesh.rad = M.get<double>(s->nt);
     s->mesh.cur = M.get<D4>(4 * (size_t)s->nt);
     s->mesh.curf = M.get<float4>(4 * (size_t)s->nt);
+    s->mesh.curl = M.get<float4>(4 * (size_t)s->nt);
+    s->mesh.plane = M.get<float4>(2 * (size_t)s->nt);
   }
   if (M.failed) return fail(DEM_ERR_NOMEM);
   s->mesh.nv = s->nv;

@@ -136,6 +136,10 @@ struct MeshDev {
   double* rad;       // [nt] element radius
   D4* cur;           // [nt][4] current vertices (absolute); .w of slot 0 = radius
   float4* curf;      // [nt][4] current vertices, shifted (float); .w of slot 0 = vertex count
+  float4* curl;      // [nt][4] low words of the shifted vertices (curf + curl = shifted
+                     // vertex to ~1e-15); .w of slots 0, 1 = radius (hi, lo)
+  float4* plane;     // [nt][2] face plane n.X = c in shifted coordinates, unit n:
+                     // (n hi, c hi), (n lo, c lo); zero for points and segments
   int32_t nv, nt;
 };
 

@@ -26,28 +26,54 @@ namespace {
 
 // ---- mesh pose: reference vertices rotated by |Omega| t about the axis ------
 
+// One thread per element: its vertices at the current pose (absolute in FP64;
+// shifted as hi + lo floats), and for triangles and rectangles the unit
+// normal and offset of its plane, split the same way.
 __global__ void k_mesh_pose(const Ctl* ctl, Params p, MeshDev mesh) {
   if (ctl->status) return;
-  const int slot = blockIdx.x * blockDim.x + threadIdx.x;  // element-vertex slot
-  if (slot >= 4 * mesh.nt) return;
-  const int k = slot >> 2, j = slot & 3;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= mesh.nt) return;
   const int4 tv = mesh.tri[k];
   const int nvk = tv.w >= 0 ? 4 : (tv.z >= 0 ? 3 : (tv.y >= 0 ? 2 : 1));
-  const int vi = j == 0 ? tv.x : (j == 1 ? tv.y : (j == 2 ? tv.z : tv.w));
-  const D4 r0 = mesh.ref[j < nvk ? vi : tv.x];
-  V3<double> pos = xyz(r0);
+  const double rad = mesh.rad[k];
   const double wn = p.omega_norm;
-  if (wn > 0.0) {
-    const double c = ctl->rot_c, s = ctl->rot_s;
-    const V3<double> ax = (1.0 / wn) * mk(p.mesh_omega[0], p.mesh_omega[1], p.mesh_omega[2]);
-    const V3<double> ctr = mk(p.mesh_center[0], p.mesh_center[1], p.mesh_center[2]);
-    const V3<double> r = pos - ctr;
-    const V3<double> rr = c * r + s * cross(ax, r) + (dot(ax, r) * (1.0 - c)) * ax;
-    pos = ctr + rr;
+  const double c = ctl->rot_c, s = ctl->rot_s;
+  const V3<double> ax =
+      wn > 0.0 ? (1.0 / wn) * mk(p.mesh_omega[0], p.mesh_omega[1], p.mesh_omega[2])
+               : mk(0.0, 0.0, 0.0);
+  const V3<double> ctr = mk(p.mesh_center[0], p.mesh_center[1], p.mesh_center[2]);
+  const V3<double> org = mk(p.origin[0], p.origin[1], p.origin[2]);
+  V3<double> X[4];  // shifted vertices
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int vi = j == 0 ? tv.x : (j == 1 ? tv.y : (j == 2 ? tv.z : tv.w));
+    V3<double> pos = xyz(mesh.ref[j < nvk ? vi : tv.x]);
+    if (wn > 0.0) {
+      const V3<double> r = pos - ctr;
+      pos = ctr + (c * r + s * cross(ax, r) + (dot(ax, r) * (1.0 - c)) * ax);
+    }
+    mesh.cur[4 * k + j] = make_D4(pos.x, pos.y, pos.z, j == 0 ? rad : 0.0);
+    X[j] = pos - org;
+    const float hx = (float)X[j].x, hy = (float)X[j].y, hz = (float)X[j].z;
+    const float rw = j == 0 ? (float)rad : (j == 1 ? (float)(rad - (double)(float)rad) : 0.f);
+    mesh.curf[4 * k + j] = make_float4(hx, hy, hz, j == 0 ? (float)nvk : 0.f);
+    mesh.curl[4 * k + j] = make_float4((float)(X[j].x - hx), (float)(X[j].y - hy),
+                                       (float)(X[j].z - hz), rw);
   }
-  mesh.cur[slot] = make_D4(pos.x, pos.y, pos.z, j == 0 ? mesh.rad[k] : 0.0);
-  mesh.curf[slot] = make_float4((float)(pos.x - p.origin[0]), (float)(pos.y - p.origin[1]),
-                                (float)(pos.z - p.origin[2]), j == 0 ? (float)nvk : 0.f);
+  float4 ph = make_float4(0.f, 0.f, 0.f, 0.f), pl = ph;
+  if (nvk >= 3) {
+    V3<double> nrm = cross(X[1] - X[0], (nvk == 4 ? X[3] : X[2]) - X[0]);
+    const double len = sqrt(dot(nrm, nrm));
+    if (len > 0.0) {
+      nrm = (1.0 / len) * nrm;
+      const double off = dot(nrm, X[0]);
+      ph = make_float4((float)nrm.x, (float)nrm.y, (float)nrm.z, (float)off);
+      pl = make_float4((float)(nrm.x - ph.x), (float)(nrm.y - ph.y), (float)(nrm.z - ph.z),
+                       (float)(off - ph.w));
+    }
+  }
+  mesh.plane[2 * k] = ph;
+  mesh.plane[2 * k + 1] = pl;
 }
 
 // Rotation of the mesh at the control block's step (after a host upload); the
@@ -110,7 +136,7 @@ __device__ __forceinline__ void acc(float& hi, float& lo, float b) {
 }
 
 #ifndef DEM_MIXED_MIN_BLOCKS
-#define DEM_MIXED_MIN_BLOCKS 6
+#define DEM_MIXED_MIN_BLOCKS 7
 #endif
 
 // sin x: Taylor polynomial to x^7 for |x| < 1/16 (the first omitted term is
@@ -120,6 +146,87 @@ __device__ __forceinline__ float sin_small(float x) {
   if (fabsf(x) >= 0.0625f) return sinf(x);
   const float x2 = x * x;
   return x * (1.f - x2 * (1.f / 6.f) * (1.f - x2 * (1.f / 20.f) * (1.f - x2 * (1.f / 42.f))));
+}
+
+// Overlap and unit normal (from the element to the particle) of particle
+// record Pt with feature `feat` of mesh element kt, in compensated FP32: the
+// element's vertices and plane are hi + lo floats in the same shifted frame as
+// the particle, so q - vertex is formed exactly (same binade) and the distance
+// keeps ~1e-14 m; the feature comes from the FP32 closest-point search (a
+// feature chosen wrongly by rounding is off by a second-order amount, since
+// neighbouring features meet with a common closest point).  Al, Bl: low words
+// of the element's first two vertex slots (their .w carry the element radius).
+__device__ __forceinline__ bool mesh_gap(const MeshDev& mesh, uint32_t kt, int feat,
+                                         const F8& Pt, const float4& Al, const float4& Bl,
+                                         float& delta, V3<float>& nh) {
+  ff dist;
+  if (feat == kFeatFace) {
+    // signed distance n . q - c with q = hi + lo, n = hi + lo, c = hi + lo
+    const float4 ph = mesh.plane[2 * kt], pl = mesh.plane[2 * kt + 1];
+    ff sd = two_prod(ph.x, Pt.hi.x);
+    sd = ff_add(sd, two_prod(ph.y, Pt.hi.y));
+    sd = ff_add(sd, two_prod(ph.z, Pt.hi.z));
+    sd = ff_add(sd, ff{-ph.w, -pl.w});
+    sd = ff_add_f(sd, (ph.x * Pt.lo.x + ph.y * Pt.lo.y + ph.z * Pt.lo.z) +
+                          (pl.x * Pt.hi.x + pl.y * Pt.hi.y + pl.z * Pt.hi.z));
+    const float sg = sd.hi >= 0.f ? 1.f : -1.f;
+    dist = ff{sg * sd.hi, sg * sd.lo};
+    nh = mk(sg * ph.x, sg * ph.y, sg * ph.z);
+  } else {
+    // e = q - (nearest point of the vertex or edge), each component hi + lo
+    const int i = feat < 4 ? feat : ((feat - 4) >> 2);
+    const float4 Vh = mesh.curf[4 * kt + i];
+    const float4 Vl = i == 0 ? Al : (i == 1 ? Bl : mesh.curl[4 * kt + i]);
+    ff ex = two_sum(Pt.hi.x - Vh.x, Pt.lo.x - Vl.x);
+    ff ey = two_sum(Pt.hi.y - Vh.y, Pt.lo.y - Vl.y);
+    ff ez = two_sum(Pt.hi.z - Vh.z, Pt.lo.z - Vl.z);
+    if (feat >= 4) {
+      const int j = (feat - 4) & 3;
+      const float4 Wh = mesh.curf[4 * kt + j];
+      const float4 Wl = j == 1 ? Bl : mesh.curl[4 * kt + j];
+      // edge direction u = W - V (hi part exact) and the foot parameter t in
+      // FP32, then once more from the residual: an error in t moves the foot
+      // along the edge, which changes the distance only to second order but
+      // would tilt the normal to first order (by the error over the distance)
+      const float uhx = Wh.x - Vh.x, uhy = Wh.y - Vh.y, uhz = Wh.z - Vh.z;
+      const float ulx = Wl.x - Vl.x, uly = Wl.y - Vl.y, ulz = Wl.z - Vl.z;
+      const V3<float> u = mk(uhx + ulx, uhy + uly, uhz + ulz);
+      const float uu = dot(u, u);
+      const float iuu = uu > 0.f ? 1.f / uu : 0.f;
+      float tt = dot(mk(ex.hi + ex.lo, ey.hi + ey.lo, ez.hi + ez.lo), u) * iuu;
+      tt = fminf(fmaxf(tt, 0.f), 1.f);
+      ex = ff_add(ex, ff_add_f(two_prod(-tt, uhx), -tt * ulx));
+      ey = ff_add(ey, ff_add_f(two_prod(-tt, uhy), -tt * uly));
+      ez = ff_add(ez, ff_add_f(two_prod(-tt, uhz), -tt * ulz));
+      if (tt > 0.f && tt < 1.f) {
+        const float t2 = dot(mk(ex.hi + ex.lo, ey.hi + ey.lo, ez.hi + ez.lo), u) * iuu;
+        ex = ff_add_f(ex, -t2 * u.x);
+        ey = ff_add_f(ey, -t2 * u.y);
+        ez = ff_add_f(ez, -t2 * u.z);
+      }
+    }
+    // |e| = sqrt(e.e), e.e in hi + lo, one correction step for the root
+    ff s2 = two_prod(ex.hi, ex.hi);
+    s2.lo = __fmaf_rn(2.f * ex.hi, ex.lo, s2.lo);
+    ff sy = two_prod(ey.hi, ey.hi);
+    sy.lo = __fmaf_rn(2.f * ey.hi, ey.lo, sy.lo);
+    ff sz = two_prod(ez.hi, ez.hi);
+    sz.lo = __fmaf_rn(2.f * ez.hi, ez.lo, sz.lo);
+    s2 = ff_add(ff_add(s2, sy), sz);
+    const float r0 = sqrtf(s2.hi);
+    if (!(r0 > 0.f)) return false;
+    const float r1 = (__fmaf_rn(-r0, r0, s2.hi) + s2.lo) / (2.f * r0);
+    dist = fast_two_sum(r0, r1);
+    const float ir = 1.f / r0;
+    nh = mk((ex.hi + ex.lo) * ir, (ey.hi + ey.lo) * ir, (ez.hi + ez.lo) * ir);
+  }
+  if (!(dist.hi > 0.f)) return false;
+  // delta = R_i + R_j - |e|
+  ff d = two_sum(Pt.hi.w, Al.w);
+  d.lo += Pt.lo.w + Bl.w;
+  d = ff_add(d, ff{-dist.hi, -dist.lo});
+  delta = d.hi + d.lo;
+  return delta >= 0.f;
 }
 
 struct MixedPolicy {
@@ -241,16 +348,14 @@ struct MixedPolicy {
     const float Rt = Pt.hi.w + Pt.lo.w;
     Acc3& F = sums.F;
     Acc3& T = sums.T;
-    // particle-triangle contacts: float pre-filter, then the geometry of the
-    // near candidates in FP64 (a triangle is large compared with the overlap)
+    // particle-element contacts: FP32 closest point as a pre-filter and to
+    // pick the nearest feature, then the overlap of the near candidates in
+    // compensated FP32 (an element is large compared with the overlap)
     if (ntc > 0) {
       const LawConst<float> cpw{p.f_Es_pw, p.f_Gs_pw, p.f_beta, p.f_mu_s, p.f_mu_r, p.f_mu_t,
                                 p.f_dt};
       HistM* hpm = static_cast<HistM*>(lb.hpm);
       const V3<float> qf = sum3(Pt);
-      const V3<double> xd = mk(p.origin[0] + ((double)Pt.hi.x + (double)Pt.lo.x),
-                               p.origin[1] + ((double)Pt.hi.y + (double)Pt.lo.y),
-                               p.origin[2] + ((double)Pt.hi.z + (double)Pt.lo.z));
       const V3<float> Om = mk(p.f_omega[0], p.f_omega[1], p.f_omega[2]);
       // particle centre relative to the rotation axis point, accurately
       const V3<float> rc = mk((Pt.hi.x - p.center_hi[0]) + (Pt.lo.x - p.center_lo[0]),
@@ -261,21 +366,16 @@ struct MixedPolicy {
         const float4 Af = mesh.curf[4 * kt], Bf = mesh.curf[4 * kt + 1],
                      Cf = mesh.curf[4 * kt + 2], Df = mesh.curf[4 * kt + 3];
         const int nvk = (int)Af.w;
+        int feat;
         const V3<float> yf =
-            closest_point_element(qf, hi3(Af), hi3(Bf), hi3(Cf), hi3(Df), nvk);
+            closest_point_element(qf, hi3(Af), hi3(Bf), hi3(Cf), hi3(Df), nvk, feat);
         const V3<float> df = qf - yf;
-        const D4 A = mesh.cur[4 * kt];
-        const float reachf = Rt + (float)A.w + p.mesh_prefilter;
+        const float4 Al = mesh.curl[4 * kt], Bl = mesh.curl[4 * kt + 1];
+        const float reachf = Rt + Al.w + p.mesh_prefilter;
         if (dot(df, df) > reachf * reachf) continue;
-        const D4 B = mesh.cur[4 * kt + 1], C = mesh.cur[4 * kt + 2], D = mesh.cur[4 * kt + 3];
-        const V3<double> pc = closest_point_element(xd, xyz(A), xyz(B), xyz(C), xyz(D), nvk);
-        const V3<double> dd = xd - pc;
-        const double distd = sqrt(dot(dd, dd));
-        const double deltad = ((double)Pt.hi.w + (double)Pt.lo.w) + A.w - distd;
-        if (deltad < 0.0 || !(distd > 0.0)) continue;
-        const float delta = (float)deltad;
-        const double idd = 1.0 / distd;
-        const V3<float> nh = mk((float)(dd.x * idd), (float)(dd.y * idd), (float)(dd.z * idd));
+        float delta;
+        V3<float> nh;
+        if (!mesh_gap(mesh, kt, feat, Pt, Al, Bl, delta, nh)) continue;
         const float ri = Rt - 0.5f * delta;
         const V3<float> vw = cross(Om, rc - ri * nh);
         HistM* hp = &hpm[(size_t)m * n + t];
@@ -387,7 +487,7 @@ struct MixedPolicy {
 
 void launch_mesh_pose(cudaStream_t st, const Ctl* ctl, const Params& p, MeshDev mesh) {
   if (mesh.nt <= 0) return;
-  k_mesh_pose<<<(unsigned)((4 * mesh.nt + 127) / 128), 128, 0, st>>>(ctl, p, mesh);
+  k_mesh_pose<<<(unsigned)((mesh.nt + 127) / 128), 128, 0, st>>>(ctl, p, mesh);
 }
 
 void launch_step(cudaStream_t st, Ctl* ctl, const Params& p, StateBufs sb, Lists L,

@@ -104,12 +104,11 @@ k_step_warp(Ctl* ctl, Params p, StateBufs sb, Lists L, MeshDev mesh, double* for
       uint32_t code = 0, u = 0;
       int tl = 0;
       if (e < E) {
-        int lo = 0, hi = 32;
-        while (hi - lo > 1) {
-          const int mid = (lo + hi) >> 1;
-          if (S.seg[mid] <= e) lo = mid;
-          else hi = mid;
-        }
+        // the particle owning entry e: largest tl with seg[tl] <= e
+        int lo = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1)
+          if (S.seg[lo + step] <= e) lo += step;
         tl = lo;
         const uint32_t k = e - S.seg[tl];
         u = lb.nbr[base + e];
