@@ -34,6 +34,18 @@
 //   * Summation order: contributions to a particle are added in ascending
 //     partner index, then ascending triangle index (single-evaluation loop
 //     over i < j, Sec. 3.2, followed by the mesh loop).
+//   * Particle spawning (Sec. 3.1, "Particle generation"): every `every` steps
+//     (the paper: every step), before the forces of that step, `attempts`
+//     attempts in sequence.  An attempt draws a radius uniformly in
+//     [r_min, r_max] unless one is carried over from a failed attempt, then a
+//     centre uniformly in the spawn box (x, y, z in that order); it is kept
+//     unless the sphere overlaps a particle (|x - x_j| < r + R_j) or a mesh
+//     element (distance < r + R_k), else its radius carries over.  Kept
+//     particles take the next caller index, v0, w0 and the identity
+//     orientation, until the capacity n_max is reached.  The uniforms are
+//     those of SplitMix64 (Steele, Lea & Flood, OOPSLA 2014) applied to
+//     seed + (k + 1) * 0x9E3779B97F4A7C15 for the k-th draw of the run, mapped
+//     to [0, 1) by their top 53 bits.
 //
 // Build: g++ -O2 -ffp-contract=off -fPIC -shared (no fused multiply-add
 // contraction, so the oracle gives the same bits on x86-64 and aarch64).
@@ -82,6 +94,17 @@ struct oracle_params {
   int32_t reserved;
 };
 
+// Spawning parameters (Sec. 3.1).  Layout must match oracle/oracle.py.
+struct oracle_spawn {
+  int64_t n_max;             // capacity: particles are never spawned beyond it
+  double lo[3], hi[3];       // spawn box corners
+  double r_min, r_max;       // radius range
+  double v0[3], w0[3];       // initial velocity and angular velocity
+  int32_t attempts;          // attempts per spawn event
+  int32_t every;             // steps between spawn events (>= 1)
+  uint64_t seed;
+};
+
 }  // extern "C"
 
 namespace {
@@ -99,7 +122,8 @@ using Key = std::pair<int64_t, int64_t>;
 
 struct Scene {
   oracle_params p;
-  int64_t n = 0;
+  int64_t n = 0;   // capacity (rows of the arrays)
+  int64_t na = 0;  // active particles: rows 0 .. na-1 (the rest have R = 0)
   std::vector<double> R, x, v, w, q;  // R[n], x/v/w[3n], q[4n] (scalar first)
   std::vector<double> F, T;           // contact force / torque sums of the last step
   int64_t nv = 0, nt = 0;             // vertices, mesh elements
@@ -109,7 +133,19 @@ struct Scene {
   std::map<Key, Hist> hist;
   int64_t step_count = 0;
   int64_t degenerate = 0;  // contacts skipped because d == 0
+  oracle_spawn sp{};       // spawning off while sp.attempts == 0
+  uint64_t draws = 0;      // uniforms drawn so far
+  double carry = -1.0;     // radius carried over from a failed attempt (< 0: none)
 };
+
+// k-th uniform of the spawn stream: SplitMix64 output for counter k, top 53 bits.
+double spawn_uniform(uint64_t seed, uint64_t k) {
+  uint64_t z = seed + (k + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z = z ^ (z >> 31);
+  return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+}
 
 // Damping factor beta(e_n) of Sec. 2.2.
 double beta_of(double e_n) {
@@ -384,10 +420,52 @@ V3 mesh_vertex(const Scene& S, int64_t k) {
   return c + rotate(r0 - c, (1.0 / wm) * Om, th);
 }
 
+// Spawn attempts of one event (Sec. 3.1), in sequence, against the particles
+// and mesh at the current step.
+void spawn_event(Scene& S) {
+  const oracle_spawn& sp = S.sp;
+  std::vector<V3> vt(S.nv);
+  for (int64_t k = 0; k < S.nv; ++k) vt[k] = mesh_vertex(S, k);
+  for (int32_t a = 0; a < sp.attempts && S.na < S.n; ++a) {
+    double r = S.carry;
+    if (r < 0.0) r = sp.r_min + spawn_uniform(sp.seed, S.draws++) * (sp.r_max - sp.r_min);
+    V3 c;
+    c.x = sp.lo[0] + spawn_uniform(sp.seed, S.draws++) * (sp.hi[0] - sp.lo[0]);
+    c.y = sp.lo[1] + spawn_uniform(sp.seed, S.draws++) * (sp.hi[1] - sp.lo[1]);
+    c.z = sp.lo[2] + spawn_uniform(sp.seed, S.draws++) * (sp.hi[2] - sp.lo[2]);
+    bool overlap = false;
+    for (int64_t j = 0; j < S.na && !overlap; ++j) {
+      const V3 d = c - load3(S.x.data(), j);
+      const double s = r + S.R[j];
+      overlap = dot(d, d) < s * s;
+    }
+    for (int64_t k = 0; k < S.nt && !overlap; ++k) {
+      const V3 d = c - closest_on_element(c, vt, &S.tri[4 * k]);
+      const double s = r + S.tri_radius[k];
+      overlap = dot(d, d) < s * s;
+    }
+    if (overlap) {
+      S.carry = r;
+      continue;
+    }
+    const int64_t i = S.na++;
+    S.R[i] = r;
+    store3(S.x.data(), i, c);
+    store3(S.v.data(), i, load3(sp.v0, 0));
+    store3(S.w.data(), i, load3(sp.w0, 0));
+    S.q[4 * i] = 1.0;
+    S.q[4 * i + 1] = S.q[4 * i + 2] = S.q[4 * i + 3] = 0.0;
+    S.carry = -1.0;
+  }
+}
+
 // One timestep: contact search and forces at t_n, then integration to t_{n+1}.
+void spawn_event(Scene& S);
+
 void step_once(Scene& S) {
   const oracle_params& p = S.p;
-  const int64_t n = S.n;
+  if (S.sp.attempts > 0 && S.step_count % S.sp.every == 0) spawn_event(S);
+  const int64_t n = S.na;  // inactive rows take part in nothing
   std::fill(S.F.begin(), S.F.end(), 0.0);
   std::fill(S.T.begin(), S.T.end(), 0.0);
   std::map<Key, Hist> next;
@@ -473,6 +551,7 @@ void* oracle_create(const oracle_params* p, int64_t n, const double* R, const do
   Scene* S = new Scene();
   S->p = *p;
   S->n = n;
+  S->na = n;
   S->R.assign(R, R + n);
   S->x.assign(x, x + 3 * n);
   S->v.assign(v, v + 3 * n);
@@ -491,6 +570,35 @@ void* oracle_create(const oracle_params* p, int64_t n, const double* R, const do
 }
 
 void oracle_destroy(void* s) { delete static_cast<Scene*>(s); }
+
+// Turn on spawning (Sec. 3.1): rows grow to the capacity sp->n_max; the new
+// rows are inactive (R = 0) until spawned.
+void oracle_set_spawn(void* s, const oracle_spawn* sp) {
+  Scene* S = static_cast<Scene*>(s);
+  S->sp = *sp;
+  if (S->sp.every < 1) S->sp.every = 1;
+  const int64_t cap = sp->n_max > S->n ? sp->n_max : S->n;
+  S->R.resize(cap, 0.0);
+  S->x.resize(3 * cap, 0.0);
+  S->v.resize(3 * cap, 0.0);
+  S->w.resize(3 * cap, 0.0);
+  S->q.resize(4 * cap, 0.0);
+  for (int64_t i = S->n; i < cap; ++i) S->q[4 * i] = 1.0;
+  S->F.resize(3 * cap, 0.0);
+  S->T.resize(3 * cap, 0.0);
+  S->n = cap;
+}
+
+int64_t oracle_active(void* s) { return static_cast<Scene*>(s)->na; }
+int64_t oracle_capacity(void* s) { return static_cast<Scene*>(s)->n; }
+uint64_t oracle_spawn_draws(void* s) { return static_cast<Scene*>(s)->draws; }
+
+void oracle_read_radii(void* s, double* R) {
+  Scene* S = static_cast<Scene*>(s);
+  std::memcpy(R, S->R.data(), sizeof(double) * S->n);
+}
+
+double oracle_spawn_uniform(uint64_t seed, uint64_t k) { return spawn_uniform(seed, k); }
 
 void oracle_step(void* s, int64_t nsteps) {
   Scene* S = static_cast<Scene*>(s);

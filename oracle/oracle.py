@@ -27,6 +27,27 @@ _I64 = ctypes.c_int64
 _P = ctypes.c_void_p
 
 
+class OracleSpawn(ctypes.Structure):
+    """Spawning parameters (Sec. 3.1); layout of oracle_spawn."""
+    _fields_ = [("n_max", _I64), ("lo", _D * 3), ("hi", _D * 3), ("r_min", _D), ("r_max", _D),
+                ("v0", _D * 3), ("w0", _D * 3), ("attempts", ctypes.c_int32),
+                ("every", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+
+
+def make_spawn(sp: dict) -> OracleSpawn:
+    o = OracleSpawn()
+    o.n_max = int(sp["n_max"])
+    o.lo[:] = [float(c) for c in sp["lo"]]
+    o.hi[:] = [float(c) for c in sp["hi"]]
+    o.r_min, o.r_max = float(sp["r_min"]), float(sp["r_max"])
+    o.v0[:] = [float(c) for c in sp.get("v0", (0.0, 0.0, 0.0))]
+    o.w0[:] = [float(c) for c in sp.get("w0", (0.0, 0.0, 0.0))]
+    o.attempts = int(sp["attempts"])
+    o.every = int(sp.get("every", 1))
+    o.seed = int(sp.get("seed", 0))
+    return o
+
+
 class OracleParams(ctypes.Structure):
     """Mirror of `oracle_params` in dem_oracle.cpp."""
 
@@ -82,6 +103,16 @@ def _load():
     lib.oracle_beta.argtypes = [_D]
     lib.oracle_contact_coeffs.argtypes = [ctypes.POINTER(OracleParams), ctypes.c_int32, _D, _D,
                                           _D, dp]
+    lib.oracle_set_spawn.argtypes = [_P, ctypes.POINTER(OracleSpawn)]
+    lib.oracle_active.restype = _I64
+    lib.oracle_active.argtypes = [_P]
+    lib.oracle_capacity.restype = _I64
+    lib.oracle_capacity.argtypes = [_P]
+    lib.oracle_spawn_draws.restype = ctypes.c_uint64
+    lib.oracle_spawn_draws.argtypes = [_P]
+    lib.oracle_read_radii.argtypes = [_P, dp]
+    lib.oracle_spawn_uniform.restype = _D
+    lib.oracle_spawn_uniform.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
     lib.oracle_sample_first_step.argtypes = [
         ctypes.POINTER(OracleParams), _I64, dp, dp, dp, dp, dp, _I64, dp, _I64,
         ctypes.POINTER(ctypes.c_int32), dp, _I64, _I64, ctypes.POINTER(_I64),
@@ -128,7 +159,7 @@ class OracleScene:
     """A DEM scene advanced by the FP64 oracle."""
 
     def __init__(self, params: dict, R, x, v=None, w=None, q=None, verts=None, tris=None,
-                 tri_radius=None, literal_sign: bool = False):
+                 tri_radius=None, literal_sign: bool = False, spawn=None):
         lib = _load()
         R = _f64(R, (-1,))
         n = R.shape[0]
@@ -157,6 +188,24 @@ class OracleScene:
                                     tb.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                                     _dptr(rb))
         self._lib = lib
+        if spawn is not None:
+            self._sp = make_spawn(spawn)
+            lib.oracle_set_spawn(self._h, ctypes.byref(self._sp))
+            self.n = int(lib.oracle_capacity(self._h))
+
+    @property
+    def active(self) -> int:
+        """Particles taking part in the dynamics (rows 0 .. active-1)."""
+        return int(self._lib.oracle_active(self._h))
+
+    @property
+    def spawn_draws(self) -> int:
+        return int(self._lib.oracle_spawn_draws(self._h))
+
+    def radii(self) -> np.ndarray:
+        R = np.empty(self.n)
+        self._lib.oracle_read_radii(self._h, _dptr(R))
+        return R
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -275,3 +324,8 @@ def sample_first_step(params: dict, R, x, v, w, q, verts, tris, tri_radius, ids,
                                  _dptr(out["F"]), _dptr(out["T"]), _dptr(out["x"]),
                                  _dptr(out["v"]), _dptr(out["w"]), _dptr(out["q"]))
     return out
+
+
+def spawn_uniform(seed: int, k: int) -> float:
+    """k-th uniform of the spawn stream (SplitMix64, top 53 bits)."""
+    return float(_load().oracle_spawn_uniform(int(seed), int(k)))
