@@ -81,11 +81,35 @@ typedef struct dem_params {
   int32_t max_neighbors; /* list capacity per particle; <= 0 selects 64 */
   int32_t max_mesh_contacts; /* mesh-element candidate capacity per particle; <= 0: 16 */
   int32_t record_forces; /* nonzero: keep per-particle contact sums for dem_read_forces */
+  /* Particle spawning (Sec. 3.1, "Particle generation"), off while
+   * spawn_attempts == 0.  The scene holds n_cap = max(n, n_max) particle rows;
+   * rows n .. n_cap-1 are inactive (radius 0, no contacts, not integrated)
+   * until spawned, in increasing row order.  Every spawn_every steps, before
+   * the forces of that step, spawn_attempts attempts run in sequence: a radius
+   * uniform in [spawn_r_min, spawn_r_max] (or the radius carried over from the
+   * last failed attempt), a centre uniform in the box [spawn_lo, spawn_hi]
+   * (x, y, z in that order); the sphere is kept unless it overlaps a particle
+   * (|x - x_j| < r + R_j) or a mesh element (distance < r + R_j), with
+   * velocity spawn_v0, angular velocity spawn_w0 and the identity
+   * orientation.  The k-th uniform of a run is the top 53 bits of SplitMix64
+   * (Steele, Lea & Flood 2014) at seed + (k + 1) * 0x9E3779B97F4A7C15.  The
+   * paper makes its attempts every step; spawn_every > 1 batches them (each
+   * event that keeps a particle costs a list rebuild). */
+  int64_t n_max;            /* particle capacity; <= n: no inactive rows */
+  double spawn_lo[3];       /* spawn box (m) */
+  double spawn_hi[3];
+  double spawn_r_min;       /* radius range (m), 0 < r_min <= r_max */
+  double spawn_r_max;
+  double spawn_v0[3];       /* initial velocity (m/s) */
+  double spawn_w0[3];       /* initial angular velocity (rad/s) */
+  int32_t spawn_attempts;   /* attempts per spawn event, 0 .. 1024 */
+  int32_t spawn_every;      /* steps between spawn events; <= 0 selects 1 */
+  uint64_t spawn_seed;
 } dem_params;
 
 /* Particles (host arrays, caller order). */
 typedef struct dem_particles {
-  int64_t n;         /* number of particles, >= 1 */
+  int64_t n;         /* number of particles, >= 1 (>= 0 with spawning on) */
   const double* R;   /* [n] radii, > 0 */
   const double* x;   /* [n][3] positions */
   const double* v;   /* [n][3] velocities; NULL = zero */
@@ -128,6 +152,8 @@ typedef struct dem_stats {
   int32_t status;         /* sticky device status (DEM_OK if none) */
   int32_t launches_per_step;    /* kernels launched in a step without a list rebuild */
   int32_t launches_per_rebuild; /* additional kernels launched in a step that rebuilds */
+  int64_t active;         /* active particles (rows 0 .. active-1); the rest await spawning */
+  int64_t capacity;       /* particle rows n_cap */
 } dem_stats;
 
 typedef struct dem_scene dem_scene;
@@ -157,9 +183,14 @@ int dem_step_timed(dem_scene* s, int64_t nsteps, double* phase_ms);
 /* Wait for the scene's stream; return the sticky device status. */
 int dem_synchronize(dem_scene* s);
 
-/* Copy the current state to host arrays in caller order; any pointer may be
- * NULL.  Synchronizes the stream. */
+/* Copy the current state to host arrays in caller order, n_cap rows (see
+ * dem_params.n_max); any pointer may be NULL.  Rows of inactive particles
+ * hold zeros and the identity orientation.  Synchronizes the stream. */
 int dem_read_state(dem_scene* s, double* x, double* v, double* w, double* q);
+
+/* Particle radii in caller order, n_cap rows (0 for inactive rows).
+ * Synchronizes the stream. */
+int dem_read_radii(dem_scene* s, double* R);
 
 /* Contact force and torque sums (no gravity or drag) of the last step, [n][3],
  * caller order.  Requires params.record_forces.  Synchronizes. */

@@ -34,6 +34,12 @@
 //   * Summation order: contributions to a particle are added in ascending
 //     partner index, then ascending triangle index (single-evaluation loop
 //     over i < j, Sec. 3.2, followed by the mesh loop).
+//   * Materials (not in the paper, which has one material): each particle may
+//     carry a material index with its own friction coefficients mu_s, mu_r,
+//     mu_t (the batched-scenes extension); a pair of particles uses the mean
+//     of the two materials' coefficients, a mesh contact the particle's.
+//     Without a material table every particle uses the coefficients of the
+//     parameters.
 //   * Particle spawning (Sec. 3.1, "Particle generation"): every `every` steps
 //     (the paper: every step), before the forces of that step, `attempts`
 //     attempts in sequence.  An attempt draws a radius uniformly in
@@ -134,6 +140,8 @@ struct Scene {
   int64_t step_count = 0;
   int64_t degenerate = 0;  // contacts skipped because d == 0
   oracle_spawn sp{};       // spawning off while sp.attempts == 0
+  std::vector<double> mat_mu;   // [3 n_mat] mu_s, mu_r, mu_t per material (empty: params)
+  std::vector<int32_t> mat;     // [n] material index per particle
   uint64_t draws = 0;      // uniforms drawn so far
   double carry = -1.0;     // radius carried over from a failed attempt (< 0: none)
 };
@@ -315,7 +323,11 @@ struct ContactOut {
 // friction (Sec. 2.2) and the history update of Sec. 2.3, for body i against
 // body j.  For a wall, j is infinitely large, stiff and heavy; its surface
 // velocity at the contact point and its angular velocity are given directly.
-ContactOut contact_law(const oracle_params& p, V3 nhat, double delta,
+struct Friction {
+  double mu_s, mu_r, mu_t;
+};
+
+ContactOut contact_law(const oracle_params& p, const Friction& mu, V3 nhat, double delta,
                        double Ri, double mi, V3 vi, V3 wi,
                        bool wall, double Rj, double mj, V3 vj, V3 wj, V3 vwall,
                        Hist& h, bool literal_sign) {
@@ -345,9 +357,9 @@ ContactOut contact_law(const oracle_params& p, V3 nhat, double delta,
   const V3 fn = -kn * un - cn * vn;
   const double fn_mag = norm(fn);
   // friction modes, each independently static or kinetic
-  const V3 fs = friction_vec(h.us, nhat, vs, ks, cs, p.mu_s, fn_mag, p.dt);
-  const V3 fr = friction_vec(h.ur, nhat, vr, kr, cr, p.mu_r, fn_mag, p.dt);
-  const double ft = friction_scalar(h.ut, vt, kt, ct, p.mu_t, fn_mag, p.dt);
+  const V3 fs = friction_vec(h.us, nhat, vs, ks, cs, mu.mu_s, fn_mag, p.dt);
+  const V3 fr = friction_vec(h.ur, nhat, vr, kr, cr, mu.mu_r, fn_mag, p.dt);
+  const double ft = friction_scalar(h.ut, vt, kt, ct, mu.mu_t, fn_mag, p.dt);
   // torques
   const V3 tau_s = ri * cross(fs, nhat);
   const V3 tau_r = Rs * cross(nhat, fr);
@@ -361,6 +373,19 @@ ContactOut contact_law(const oracle_params& p, V3 nhat, double delta,
 }
 
 double mass_of(const oracle_params& p, double R) { return 4.0 / 3.0 * M_PI * p.rho * R * R * R; }
+
+// Friction coefficients of particle i's material (the parameters' without a table).
+Friction friction_of(const Scene& S, int64_t i) {
+  if (S.mat_mu.empty()) return Friction{S.p.mu_s, S.p.mu_r, S.p.mu_t};
+  const double* m = &S.mat_mu[3 * (size_t)S.mat[i]];
+  return Friction{m[0], m[1], m[2]};
+}
+
+// A pair of particles: the mean of the two materials' coefficients.
+Friction friction_of_pair(const Scene& S, int64_t i, int64_t j) {
+  const Friction a = friction_of(S, i), b = friction_of(S, j);
+  return Friction{(a.mu_s + b.mu_s) / 2.0, (a.mu_r + b.mu_r) / 2.0, (a.mu_t + b.mu_t) / 2.0};
+}
 
 // Hamilton product (Sec. 2.3).
 void qmul(const double* a, const double* b, double* out) {
@@ -486,7 +511,8 @@ void step_once(Scene& S) {
       auto it = S.hist.find(Key(i, j));
       if (it != S.hist.end()) h = it->second;
       const double Rj = S.R[j];
-      ContactOut o = contact_law(p, nhat, delta, Ri, mi, vi, wi, false, Rj, mass_of(p, Rj),
+      ContactOut o = contact_law(p, friction_of_pair(S, i, j), nhat, delta, Ri, mi, vi, wi,
+                                 false, Rj, mass_of(p, Rj),
                                  load3(S.v.data(), j), load3(S.w.data(), j), v3(0, 0, 0), h,
                                  p.literal_sign != 0);
       store3(S.F.data(), i, load3(S.F.data(), i) + o.f);
@@ -520,7 +546,8 @@ void step_once(Scene& S) {
         const double ri = Ri - delta / 2.0;
         const V3 xc = xi - ri * nhat;  // contact point
         const V3 vwall = cross(Om, xc - c);
-        ContactOut o = contact_law(p, nhat, delta, Ri, mi, vi, wi, true, INFINITY, INFINITY,
+        ContactOut o = contact_law(p, friction_of(S, i), nhat, delta, Ri, mi, vi, wi, true,
+                                   INFINITY, INFINITY,
                                    v3(0, 0, 0), Om, vwall, h, false);
         store3(S.F.data(), i, load3(S.F.data(), i) + o.f);
         store3(S.T.data(), i, load3(S.T.data(), i) + o.tau_i);
@@ -584,12 +611,22 @@ void oracle_set_spawn(void* s, const oracle_spawn* sp) {
   S->w.resize(3 * cap, 0.0);
   S->q.resize(4 * cap, 0.0);
   for (int64_t i = S->n; i < cap; ++i) S->q[4 * i] = 1.0;
+  if (!S->mat.empty()) S->mat.resize(cap, 0);  // spawned particles: material 0
   S->F.resize(3 * cap, 0.0);
   S->T.resize(3 * cap, 0.0);
   S->n = cap;
 }
 
 int64_t oracle_active(void* s) { return static_cast<Scene*>(s)->na; }
+
+// Friction per material (not in the paper): mu[3k..3k+2] = mu_s, mu_r, mu_t of
+// material k; mat[i] = material of particle i (rows beyond n take material 0).
+void oracle_set_materials(void* s, int32_t n_mat, const double* mu, const int32_t* mat) {
+  Scene* S = static_cast<Scene*>(s);
+  S->mat_mu.assign(mu, mu + 3 * (size_t)n_mat);
+  S->mat.assign(S->n, 0);
+  for (int64_t i = 0; i < S->n; ++i) S->mat[i] = mat ? mat[i] : 0;
+}
 int64_t oracle_capacity(void* s) { return static_cast<Scene*>(s)->n; }
 uint64_t oracle_spawn_draws(void* s) { return static_cast<Scene*>(s)->draws; }
 
@@ -730,7 +767,8 @@ void oracle_sample_first_step(const oracle_params* p, int64_t n, const double* R
       if (delta < 0.0 || !(dist > 0.0)) continue;
       const V3 nhat = (1.0 / dist) * d;
       Hist h;
-      ContactOut o = contact_law(*p, nhat, delta, R[lo], mass_of(*p, R[lo]), load3(v, lo),
+      ContactOut o = contact_law(*p, Friction{p->mu_s, p->mu_r, p->mu_t}, nhat, delta, R[lo],
+                                 mass_of(*p, R[lo]), load3(v, lo),
                                  load3(w, lo), false, R[hi], mass_of(*p, R[hi]), load3(v, hi),
                                  load3(w, hi), v3(0, 0, 0), h, p->literal_sign != 0);
       if (i == lo) {
@@ -751,7 +789,8 @@ void oracle_sample_first_step(const oracle_params* p, int64_t n, const double* R
       Hist h;
       const double ri = Ri - delta / 2.0;
       const V3 xc = xi - ri * nhat;
-      ContactOut o = contact_law(*p, nhat, delta, Ri, mi, vi, wi, true, INFINITY, INFINITY,
+      ContactOut o = contact_law(*p, Friction{p->mu_s, p->mu_r, p->mu_t}, nhat, delta, Ri, mi,
+                                 vi, wi, true, INFINITY, INFINITY,
                                  v3(0, 0, 0), Om, cross(Om, xc - c), h, false);
       F = F + o.f;
       T = T + o.tau_i;

@@ -104,6 +104,7 @@ def _load():
     lib.oracle_contact_coeffs.argtypes = [ctypes.POINTER(OracleParams), ctypes.c_int32, _D, _D,
                                           _D, dp]
     lib.oracle_set_spawn.argtypes = [_P, ctypes.POINTER(OracleSpawn)]
+    lib.oracle_set_materials.argtypes = [_P, ctypes.c_int32, dp, ctypes.POINTER(ctypes.c_int32)]
     lib.oracle_active.restype = _I64
     lib.oracle_active.argtypes = [_P]
     lib.oracle_capacity.restype = _I64
@@ -159,7 +160,8 @@ class OracleScene:
     """A DEM scene advanced by the FP64 oracle."""
 
     def __init__(self, params: dict, R, x, v=None, w=None, q=None, verts=None, tris=None,
-                 tri_radius=None, literal_sign: bool = False, spawn=None):
+                 tri_radius=None, literal_sign: bool = False, spawn=None, material=None,
+                 material_mu=None):
         lib = _load()
         R = _f64(R, (-1,))
         n = R.shape[0]
@@ -188,6 +190,13 @@ class OracleScene:
                                     tb.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                                     _dptr(rb))
         self._lib = lib
+        if material_mu is not None:
+            # friction per material: (n_mat, 3) mu_s, mu_r, mu_t; material[i] per particle
+            mu = _f64(material_mu, (-1, 3))
+            mat = np.zeros(n, dtype=np.int32) if material is None else np.ascontiguousarray(
+                np.asarray(material, dtype=np.int32).reshape(n))
+            lib.oracle_set_materials(self._h, mu.shape[0], _dptr(mu),
+                                     mat.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
         if spawn is not None:
             self._sp = make_spawn(spawn)
             lib.oracle_set_spawn(self._h, ctypes.byref(self._sp))

@@ -125,6 +125,7 @@ struct dem_scene {
   Params p{};
   int64_t n = 0;
   int32_t nv = 0, nt = 0;
+  int64_t n_init = 0;     // particles active at creation (the rest await spawning)
   size_t hist_bytes = 0;  // 64 (FP64) or 32 (mixed)
   Ctl* ctl = nullptr;
   StateBufs sb{};
@@ -167,8 +168,23 @@ int validate(const dem_params* pr, const dem_particles* pa, const dem_mesh* me) 
   if (!(pr->dt > 0)) return DEM_ERR_INVALID;
   if (pr->precision != DEM_FP64 && pr->precision != DEM_MIXED) return DEM_ERR_INVALID;
   if (pr->max_neighbors > 64 || pr->max_mesh_contacts > 255) return DEM_ERR_INVALID;
-  if (pa->n < 1 || pa->n > (int64_t)0x7fffffff / 2) return DEM_ERR_INVALID;
-  if (!pa->R || !pa->x) return DEM_ERR_INVALID;
+  // spawning (Sec. 3.1)
+  const bool spawn = pr->spawn_attempts != 0;
+  if (pr->spawn_attempts < 0 || pr->spawn_attempts > kSpawnMaxAttempts) return DEM_ERR_INVALID;
+  if (pr->n_max > (int64_t)0x7fffffff / 2) return DEM_ERR_INVALID;
+  if (spawn) {
+    const double sp[] = {pr->spawn_lo[0], pr->spawn_lo[1], pr->spawn_lo[2], pr->spawn_hi[0],
+                         pr->spawn_hi[1], pr->spawn_hi[2], pr->spawn_r_min, pr->spawn_r_max,
+                         pr->spawn_v0[0], pr->spawn_v0[1], pr->spawn_v0[2], pr->spawn_w0[0],
+                         pr->spawn_w0[1], pr->spawn_w0[2]};
+    if (!finite_all(sp, sizeof sp / sizeof sp[0])) return DEM_ERR_INVALID;
+    if (!(pr->spawn_r_min > 0) || !(pr->spawn_r_max >= pr->spawn_r_min)) return DEM_ERR_INVALID;
+    for (int a = 0; a < 3; ++a)
+      if (!(pr->spawn_lo[a] <= pr->spawn_hi[a])) return DEM_ERR_INVALID;
+    if (pr->n_max < 1) return DEM_ERR_INVALID;
+  }
+  if (pa->n < (spawn ? 0 : 1) || pa->n > (int64_t)0x7fffffff / 2) return DEM_ERR_INVALID;
+  if (pa->n > 0 && (!pa->R || !pa->x)) return DEM_ERR_INVALID;
   const int64_t n = pa->n;
   for (int64_t i = 0; i < n; ++i)
     if (!(pa->R[i] > 0) || !std::isfinite(pa->R[i])) return DEM_ERR_INVALID;
@@ -197,6 +213,7 @@ inline void split(double a, float& hi, float& lo) {
 void enqueue_step(dem_scene* s) {
   if (!s->static_mesh) launch_mesh_pose(s->stream, s->ctl, s->p, s->mesh);
   launch_rebuild(s->stream, s->ctl, s->p, s->sb, s->L, s->bb, s->mesh);
+  launch_spawn(s->stream, s->ctl, s->p, s->sb, s->bb, s->mesh);
   launch_step(s->stream, s->ctl, s->p, s->sb, s->L, s->mesh, s->forces);
   launch_advance(s->stream, s->ctl, s->p);
 }
@@ -237,6 +254,7 @@ cudaError_t enqueue_step_conditional(dem_scene* s) {
   e = cudaStreamUpdateCaptureDependencies(s->stream, &node, nullptr, 1,
                                           cudaStreamSetCaptureDependencies);
   if (e != cudaSuccess) return e;
+  launch_spawn(s->stream, s->ctl, s->p, s->sb, s->bb, s->mesh);
   launch_step(s->stream, s->ctl, s->p, s->sb, s->L, s->mesh, s->forces);
   launch_advance(s->stream, s->ctl, s->p);
   return cudaSuccess;
@@ -461,7 +479,8 @@ int install_contacts(dem_scene* s, const std::vector<ContactRow>& rows, uint32_t
 // Upload a state given in caller order (slot = caller index) into buffer 0,
 // reset the control block to (step, lphase 0), and request a rebuild.
 int upload_state(dem_scene* s, const double* x, const double* v, const double* w,
-                 const double* q, const double* R, int64_t step) {
+                 const double* q, const double* R, int64_t step, int64_t n_active,
+                 double spawn_carry, uint64_t spawn_draws) {
   const int64_t n = s->n;
   const double rho = s->p.rho;
   if (s->p.mixed) {
@@ -476,11 +495,11 @@ int upload_state(dem_scene* s, const double* x, const double* v, const double* w
       split(v ? v[3 * i + 1] : 0.0, V[i].hi.y, V[i].lo.y);
       split(v ? v[3 * i + 2] : 0.0, V[i].hi.z, V[i].lo.z);
       V[i].hi.w = (float)m;
-      V[i].lo.w = (float)(1.0 / m);  // inverse mass, for the contact law
+      V[i].lo.w = R[i] > 0 ? (float)(1.0 / m) : 0.f;  // inverse mass, for the contact law
       split(w ? w[3 * i] : 0.0, W[i].hi.x, W[i].lo.x);
       split(w ? w[3 * i + 1] : 0.0, W[i].hi.y, W[i].lo.y);
       split(w ? w[3 * i + 2] : 0.0, W[i].hi.z, W[i].lo.z);
-      W[i].hi.w = (float)(1.0 / R[i]);  // inverse radius
+      W[i].hi.w = R[i] > 0 ? (float)(1.0 / R[i]) : 0.f;  // inverse radius
       W[i].lo.w = 0.f;
       split(q ? q[4 * i] : 1.0, Q[i].hi.x, Q[i].lo.x);
       split(q ? q[4 * i + 1] : 0.0, Q[i].hi.y, Q[i].lo.y);
@@ -516,6 +535,9 @@ int upload_state(dem_scene* s, const double* x, const double* v, const double* w
   Ctl c{};
   c.step = step;
   c.rebuild = 1;
+  c.n_active = (uint32_t)n_active;
+  c.spawn_carry = spawn_carry;
+  c.spawn_draws = spawn_draws;
   DEM_TRY(cudaMemcpy(s->ctl, &c, sizeof c, cudaMemcpyHostToDevice));
   launch_set_pose(s->stream, s->ctl, s->p);  // rotation of this step, on the device
   return DEM_OK;
@@ -577,8 +599,11 @@ int dem_scene_create(const dem_params* params, const dem_particles* parts, const
     s->aux = nullptr;
   }
   s->user = *params;
-  const int64_t n = parts->n;
+  const int64_t n_init = parts->n;  // active at creation; rows n_init .. n-1 await spawning
+  const bool spawning = params->spawn_attempts > 0;
+  const int64_t n = std::max(n_init, params->n_max);
   s->n = n;
+  s->n_init = n_init;
   const bool has_mesh = !et.el.empty();
   s->nt = (int32_t)et.el.size();
   s->nv = has_mesh ? (int32_t)mesh->n_vert : 0;
@@ -629,12 +654,27 @@ int dem_scene_create(const dem_params* params, const dem_particles* parts, const
   p.cap = params->max_neighbors > 0 ? params->max_neighbors : 64;
   p.capm = params->max_mesh_contacts > 0 ? params->max_mesh_contacts : 16;
   s->hist_bytes = p.mixed ? sizeof(HistM) : sizeof(HistD);
+  p.sp_attempts = spawning ? params->spawn_attempts : 0;
+  p.sp_every = params->spawn_every > 0 ? params->spawn_every : 1;
+  p.sp_seed = params->spawn_seed;
+  p.sp_rmin = params->spawn_r_min;
+  p.sp_rmax = params->spawn_r_max;
+  for (int a = 0; a < 3; ++a) {
+    p.sp_lo[a] = params->spawn_lo[a];
+    p.sp_hi[a] = params->spawn_hi[a];
+    p.sp_v0[a] = params->spawn_v0[a];
+    p.sp_w0[a] = params->spawn_w0[a];
+  }
 
   // radii, skin, domain
   double rmax = 0, rmin = INFINITY;
-  for (int64_t i = 0; i < n; ++i) {
+  for (int64_t i = 0; i < n_init; ++i) {
     rmax = std::max(rmax, parts->R[i]);
     rmin = std::min(rmin, parts->R[i]);
+  }
+  if (spawning) {
+    rmax = std::max(rmax, params->spawn_r_max);
+    rmin = std::min(rmin, params->spawn_r_min);
   }
   const double skin = params->skin > 0 ? params->skin : 0.25 * rmax;
   double lo[3], hi[3];
@@ -645,10 +685,15 @@ int dem_scene_create(const dem_params* params, const dem_particles* parts, const
     for (int a = 0; a < 3; ++a) lo[a] = params->domain_lo[a], hi[a] = params->domain_hi[a];
   } else {
     for (int a = 0; a < 3; ++a) lo[a] = INFINITY, hi[a] = -INFINITY;
-    for (int64_t i = 0; i < n; ++i)
+    for (int64_t i = 0; i < n_init; ++i)
       for (int a = 0; a < 3; ++a) {
         lo[a] = std::min(lo[a], parts->x[3 * i + a]);
         hi[a] = std::max(hi[a], parts->x[3 * i + a]);
+      }
+    if (spawning)
+      for (int a = 0; a < 3; ++a) {
+        lo[a] = std::min(lo[a], params->spawn_lo[a]);
+        hi[a] = std::max(hi[a], params->spawn_hi[a]);
       }
     double mrad = 0;
     if (has_mesh) {
@@ -766,9 +811,10 @@ int dem_scene_create(const dem_params* params, const dem_particles* parts, const
   s->bb.key = M.get<uint32_t>(n);
   s->bb.local = M.get<uint32_t>(n);
   s->bb.order = M.get<uint32_t>(n);
-  s->bb.cell_count = M.get<uint32_t>(ncells);
-  s->bb.cell_start = M.get<uint32_t>(ncells + 1);
-  s->bb.block_sums = M.get<uint32_t>(scan_block_sums_size(std::max<int64_t>(ncells, n)) + 1);
+  // one cell more than the grid: inactive particles (awaiting spawning)
+  s->bb.cell_count = M.get<uint32_t>(ncells + 1);
+  s->bb.cell_start = M.get<uint32_t>(ncells + 2);
+  s->bb.block_sums = M.get<uint32_t>(scan_block_sums_size(std::max<int64_t>(ncells + 1, n)) + 1);
   s->bb.tmp_nbr = M.get<uint32_t>((size_t)p.cap * n);
   s->bb.tmp_cnt = M.get<uint32_t>(n);
   s->bb.tmp_offs = M.get<uint32_t>(n + 1);
@@ -826,7 +872,22 @@ int dem_scene_create(const dem_params* params, const dem_particles* parts, const
   // kernels per step: mesh pose, [decide], rebuild (prep, clear, count, 3 scan,
   // scatter, cell sort, permute, [mesh: clear, count, 3 scan, check, clear, fill,
   // sort], list build, 3 scan, compact, end), step, advance -- see dem_get_stats
-  rc = upload_state(s, parts->x, parts->v, parts->w, parts->q, parts->R, 0);
+  {
+    // capacity rows: the given particles, then inactive rows (radius 0)
+    std::vector<double> R(n, 0.0), x(3 * n, 0.0), v(3 * n, 0.0), w(3 * n, 0.0), q(4 * n, 0.0);
+    for (int64_t i = 0; i < n; ++i) q[4 * i] = 1.0;
+    for (int64_t i = 0; i < n_init; ++i) {
+      R[i] = parts->R[i];
+      for (int a = 0; a < 3; ++a) {
+        x[3 * i + a] = parts->x[3 * i + a];
+        if (parts->v) v[3 * i + a] = parts->v[3 * i + a];
+        if (parts->w) w[3 * i + a] = parts->w[3 * i + a];
+      }
+      if (parts->q)
+        for (int a = 0; a < 4; ++a) q[4 * i + a] = parts->q[4 * i + a];
+    }
+    rc = upload_state(s, x.data(), v.data(), w.data(), q.data(), R.data(), 0, n_init, -1.0, 0);
+  }
   if (rc != DEM_OK) return fail(rc);
   // pose at step 0 (a static mesh keeps it)
   launch_mesh_pose(s->stream, s->ctl, s->p, s->mesh);
@@ -868,6 +929,7 @@ int dem_step_timed(dem_scene* s, int64_t nsteps, double* phase_ms) {
     if (!s->static_mesh) launch_mesh_pose(s->stream, s->ctl, s->p, s->mesh);
     cudaEventRecord(ev[1], s->stream);
     launch_rebuild(s->stream, s->ctl, s->p, s->sb, s->L, s->bb, s->mesh);
+    launch_spawn(s->stream, s->ctl, s->p, s->sb, s->bb, s->mesh);
     cudaEventRecord(ev[2], s->stream);
     launch_step(s->stream, s->ctl, s->p, s->sb, s->L, s->mesh, s->forces);
     cudaEventRecord(ev[3], s->stream);
@@ -884,6 +946,19 @@ int dem_step_timed(dem_scene* s, int64_t nsteps, double* phase_ms) {
   for (int i = 0; i < 4; ++i) phase_ms[i] += acc[i];
   if (rc != DEM_OK) return rc;
   return dem_synchronize(s);
+}
+
+int dem_read_radii(dem_scene* s, double* R) {
+  if (!s || !R) return DEM_ERR_INVALID;
+  Ctl c;
+  int rc = read_ctl(s, &c);
+  if (rc != DEM_OK) return rc;
+  HostState h;
+  rc = fetch_state(s, c, h);
+  if (rc != DEM_OK) return rc;
+  for (int64_t t = 0; t < s->n; ++t)
+    R[h.gid[t]] = s->p.mixed ? (double)h.Pm[t].hi.w + (double)h.Pm[t].lo.w : h.Pd[t].w;
+  return (int)c.status;
 }
 
 int dem_synchronize(dem_scene* s) {
@@ -905,6 +980,16 @@ int dem_read_state(dem_scene* s, double* x, double* v, double* w, double* q) {
   const int64_t n = s->n;
   for (int64_t t = 0; t < n; ++t) {
     const int64_t i = h.gid[t];
+    const bool inactive = s->p.mixed ? (h.Pm[t].hi.w == 0.f) : (h.Pd[t].w == 0.0);
+    if (inactive) {  // awaiting spawning
+      for (int a = 0; a < 3; ++a) {
+        if (x) x[3 * i + a] = 0.0;
+        if (v) v[3 * i + a] = 0.0;
+        if (w) w[3 * i + a] = 0.0;
+      }
+      if (q) q[4 * i] = 1.0, q[4 * i + 1] = q[4 * i + 2] = q[4 * i + 3] = 0.0;
+      continue;
+    }
     if (s->p.mixed) {
       const F8 &P = h.Pm[t], &V = h.Vm[t], &W = h.Wm[t], &Q = h.Qm[t];
       if (x) {
@@ -990,8 +1075,10 @@ int dem_get_stats(dem_scene* s, dem_stats* out) {
   out->mesh_candidates = c.mesh_candidates;
   out->max_list_len = (int32_t)c.max_list_len;
   out->status = (int32_t)c.status;
+  out->active = c.n_active;
+  out->capacity = s->n;
   const int32_t rebuild_launches = 15 + (s->nt > 0 ? 9 : 0);
-  const int32_t base = (s->static_mesh ? 0 : 1) + 2;
+  const int32_t base = (s->static_mesh ? 0 : 1) + 2 + (s->p.sp_attempts > 0 ? 1 : 0);
   if (s->conditional_graphs) {
     out->launches_per_step = base + 1;
     out->launches_per_rebuild = rebuild_launches;
@@ -1003,7 +1090,8 @@ int dem_get_stats(dem_scene* s, dem_stats* out) {
 }
 
 // Save format (little-endian, native struct layout):
-//   u64 magic, u64 version, i64 n, i64 mesh elements, dem_params, i64 step,
+//   u64 magic, u64 version (2), i64 n (rows), i64 mesh elements, dem_params,
+//   i64 step, i64 active particles, u64 spawn draws, f64 carried spawn radius,
 //   n records P, V, W, Q in caller order (D4 or F8 by precision),
 //   n radii (double), i64 m, m x (i64 i, i64 j, double h[7]).
 static const uint64_t kMagic = 0x4d45445f42503347ull;  // "G3PB_DEM"
@@ -1022,7 +1110,7 @@ int dem_save(dem_scene* s, void* buf, size_t* len) {
   if (rc != DEM_OK) return rc;
   const int64_t n = s->n;
   const size_t rec = s->p.mixed ? sizeof(F8) : sizeof(D4);
-  const size_t need = 8 * 4 + sizeof(dem_params) + 8 + 4 * n * rec + 8 * n + 8 +
+  const size_t need = 8 * 4 + sizeof(dem_params) + 8 + 24 + 4 * n * rec + 8 * n + 8 +
                       rows.size() * (16 + 56);
   if (!buf) {
     *len = need;
@@ -1037,14 +1125,18 @@ int dem_save(dem_scene* s, void* buf, size_t* len) {
     std::memcpy(o, src, b);
     o += b;
   };
-  const uint64_t ver = 1;
+  const uint64_t ver = 2;
   const int64_t nt = s->nt;
+  const int64_t na = c.n_active;
   put(&kMagic, 8);
   put(&ver, 8);
   put(&n, 8);
   put(&nt, 8);
   put(&s->user, sizeof(dem_params));
   put(&c.step, 8);
+  put(&na, 8);
+  put(&c.spawn_draws, 8);
+  put(&c.spawn_carry, 8);
   // records in caller order
   std::vector<unsigned char> tmp(n * rec);
   for (int part = 0; part < 4; ++part) {
@@ -1092,8 +1184,14 @@ int dem_load(dem_scene* s, const void* buf, size_t len) {
   int64_t n, nt, step;
   dem_params up;
   if (!get(&magic, 8) || !get(&ver, 8) || !get(&n, 8) || !get(&nt, 8)) return DEM_ERR_INVALID;
-  if (magic != kMagic || ver != 1 || n != s->n || nt != s->nt) return DEM_ERR_INVALID;
-  if (!get(&up, sizeof up) || !get(&step, 8)) return DEM_ERR_INVALID;
+  if (magic != kMagic || ver != 2 || n != s->n || nt != s->nt) return DEM_ERR_INVALID;
+  int64_t na;
+  uint64_t draws;
+  double carry;
+  if (!get(&up, sizeof up) || !get(&step, 8) || !get(&na, 8) || !get(&draws, 8) ||
+      !get(&carry, 8))
+    return DEM_ERR_INVALID;
+  if (na < 0 || na > n) return DEM_ERR_INVALID;
   if (up.precision != s->user.precision) return DEM_ERR_INVALID;
   const size_t rec = s->p.mixed ? sizeof(F8) : sizeof(D4);
   if (in + 4 * n * rec + 8 * n + 8 > end) return DEM_ERR_INVALID;
@@ -1122,6 +1220,9 @@ int dem_load(dem_scene* s, const void* buf, size_t len) {
   Ctl c{};
   c.step = step;
   c.rebuild = 1;
+  c.n_active = (uint32_t)na;
+  c.spawn_draws = draws;
+  c.spawn_carry = carry;
   DEM_TRY(cudaMemcpy(s->ctl, &c, sizeof c, cudaMemcpyHostToDevice));
   launch_set_pose(s->stream, s->ctl, s->p);
   launch_mesh_pose(s->stream, s->ctl, s->p, s->mesh);

@@ -36,7 +36,9 @@ struct Ctl {
   uint32_t list_entries;     // directed candidate entries of the current list
   uint32_t mesh_candidates;
   uint32_t max_list_len;
-  uint32_t pad0;
+  uint32_t n_active;     // particles in the dynamics: caller indices 0 .. n_active-1
+  double spawn_carry;    // radius carried over from a failed spawn attempt (< 0: none)
+  uint64_t spawn_draws;  // uniforms of the spawn stream drawn so far
 };
 
 // Parameters the kernels need, passed by value.
@@ -73,7 +75,16 @@ struct Params {
   int32_t n_tri;
   int32_t record_forces;
   int32_t mixed;
+  // spawning (n above is the capacity; see Ctl::n_active)
+  double sp_lo[3], sp_hi[3];
+  double sp_rmin, sp_rmax;
+  double sp_v0[3], sp_w0[3];
+  uint64_t sp_seed;
+  int32_t sp_attempts;      // 0: spawning off
+  int32_t sp_every;
 };
+
+constexpr int kSpawnMaxAttempts = 1024;
 
 // Dynamic state, double precision: four 32-byte records per particle.
 struct StateD {
@@ -200,6 +211,8 @@ __device__ __forceinline__ ListBuf list_of(const Lists& L, uint32_t b) {
 #endif
 
 // Kernel launch helpers implemented in the .cu files.
+void launch_spawn(cudaStream_t st, Ctl* ctl, const Params& p, StateBufs sb, BinBuf bb,
+                  MeshDev mesh);
 void launch_mesh_pose(cudaStream_t st, const Ctl* ctl, const Params& p, MeshDev mesh);
 void launch_rebuild(cudaStream_t st, Ctl* ctl, const Params& p, StateBufs sb, Lists L,
                     BinBuf bb, MeshDev mesh);

@@ -53,12 +53,22 @@ __global__ void k_clear(const Ctl* ctl, uint32_t* a, int64_t n) {
 }
 
 // key = cell of each particle; local = its arrival index in the cell.
+// Inactive particles (radius 0, awaiting spawning) go to an extra cell after
+// the grid that no search visits, in caller order: they are caller indices
+// n_active .. n-1, so each one's slot is its caller index.
 __global__ void __launch_bounds__(kThreads)
-k_bin_count(const Ctl* ctl, Params p, StateBufs sb, BinBuf bb) {
+k_bin_count(const Ctl* ctl, Params p, StateBufs sb, BinBuf bb, Lists L) {
   if (!rebuilding(ctl)) return;
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= p.n) return;
   const float4 X = posf_of(p, buf_of(sb.P, ctl->phase & 1u), s);
+  if (X.w == 0.f) {
+    const uint32_t c = (uint32_t)p.ncells;
+    bb.key[s] = c;
+    bb.local[s] = list_of(L, ctl->lphase & 1u).gid[s] - ctl->n_active;
+    atomicAdd(&bb.cell_count[c], 1u);
+    return;
+  }
   const uint32_t c = cell_index(p, cell_coords(p, X.x, X.y, X.z));
   bb.key[s] = c;
   bb.local[s] = atomicAdd(&bb.cell_count[c], 1u);
@@ -228,6 +238,11 @@ k_list_build(Ctl* ctl, Params p, BinBuf bb, Lists L, MeshDev mesh) {
   const ListBuf ln = list_of(L, (ctl->lphase & 1u) ^ 1u);
   const int n = p.n;
   const float4 X = ln.posf[t];
+  if (X.w == 0.f) {  // inactive: no list, no mesh candidates
+    bb.tmp_cnt[t] = 0u;
+    ln.meta[t] = 0u;
+    return;
+  }
   const uint32_t gt = ln.gid[t];
   const int3 c = cell_coords(p, X.x, X.y, X.z);
 
@@ -397,9 +412,9 @@ void launch_rebuild(cudaStream_t st, Ctl* ctl, const Params& p, StateBufs sb, Li
   const unsigned nb = blocks_for(p.n, kThreads);
   const unsigned gcells = (unsigned)std::min<int64_t>(blocks_for(p.ncells, kThreads), 152 * 16);
   k_rebuild_prep<<<1, 1, 0, st>>>(ctl);
-  k_clear<<<gcells, kThreads, 0, st>>>(ctl, bb.cell_count, p.ncells);
-  k_bin_count<<<nb, kThreads, 0, st>>>(ctl, p, sb, bb);
-  launch_scan(st, ctl, bb.cell_count, bb.cell_start, p.ncells, bb.block_sums);
+  k_clear<<<gcells, kThreads, 0, st>>>(ctl, bb.cell_count, p.ncells + 1);
+  k_bin_count<<<nb, kThreads, 0, st>>>(ctl, p, sb, bb, L);
+  launch_scan(st, ctl, bb.cell_count, bb.cell_start, p.ncells + 1, bb.block_sums);
   k_scatter<<<nb, kThreads, 0, st>>>(ctl, p, bb);
   k_cell_sort<<<gcells, kThreads, 0, st>>>(ctl, p, bb, L);
   if (p.mixed)

@@ -346,6 +346,15 @@ struct MixedPolicy {
     const int ntc = (int)ntc_u;
     const F8* Q = static_cast<const F8*>(buf_of(sb.Q, ph));
     const float Rt = Pt.hi.w + Pt.lo.w;
+    if (Rt == 0.f) {  // inactive (awaiting spawning): carried over unchanged
+      static_cast<F8*>(buf_of(sb.P, ph ^ 1u))[t] = Pt;
+      static_cast<F8*>(buf_of(sb.V, ph ^ 1u))[t] = Vt;
+      static_cast<F8*>(buf_of(sb.W, ph ^ 1u))[t] = Wt;
+      static_cast<F8*>(buf_of(sb.Q, ph ^ 1u))[t] = Q[t];
+      if (p.record_forces)
+        for (int c = 0; c < 6; ++c) forces[6 * (size_t)t + c] = 0.0;
+      return;
+    }
     Acc3& F = sums.F;
     Acc3& T = sums.T;
     // particle-element contacts: FP32 closest point as a pre-filter and to

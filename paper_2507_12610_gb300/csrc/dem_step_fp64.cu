@@ -116,6 +116,15 @@ struct Fp64Policy {
     const int n = p.n;
     const int ntc = (int)ntc_u;
     const D4* Q = static_cast<const D4*>(buf_of(sb.Q, ph));
+    if (Pt.w == 0.0) {  // inactive (awaiting spawning): carried over unchanged
+      static_cast<D4*>(buf_of(sb.P, ph ^ 1u))[t] = Pt;
+      static_cast<D4*>(buf_of(sb.V, ph ^ 1u))[t] = Vt;
+      static_cast<D4*>(buf_of(sb.W, ph ^ 1u))[t] = Wt;
+      static_cast<D4*>(buf_of(sb.Q, ph ^ 1u))[t] = Q[t];
+      if (p.record_forces)
+        for (int c = 0; c < 6; ++c) forces[6 * (size_t)t + c] = 0.0;
+      return;
+    }
     V3<double>& F = sums.F;
     V3<double>& T = sums.T;
     // particle-triangle contacts

@@ -36,7 +36,7 @@ _DP = ctypes.POINTER(ctypes.c_double)
 EXPORTS = ("dem_scene_create", "dem_step", "dem_synchronize", "dem_read_state",
            "dem_read_forces", "dem_read_contacts", "dem_get_stats", "dem_save", "dem_load",
            "dem_scene_destroy", "dem_status_string", "dem_step_timed",
-           "dem_contact_forces_noalloc")
+           "dem_contact_forces_noalloc", "dem_read_radii")
 
 
 class dem_params(ctypes.Structure):
@@ -45,7 +45,10 @@ class dem_params(ctypes.Structure):
                 ("mesh_omega", _D * 3), ("mesh_center", _D * 3), ("skin", _D),
                 ("domain_lo", _D * 3), ("domain_hi", _D * 3), ("precision", _I32),
                 ("max_neighbors", _I32), ("max_mesh_contacts", _I32),
-                ("record_forces", _I32)]
+                ("record_forces", _I32), ("n_max", _I64), ("spawn_lo", _D * 3),
+                ("spawn_hi", _D * 3), ("spawn_r_min", _D), ("spawn_r_max", _D),
+                ("spawn_v0", _D * 3), ("spawn_w0", _D * 3), ("spawn_attempts", _I32),
+                ("spawn_every", _I32), ("spawn_seed", ctypes.c_uint64)]
 
 
 class dem_particles(ctypes.Structure):
@@ -63,7 +66,7 @@ class dem_stats(ctypes.Structure):
     _fields_ = [("steps", _I64), ("rebuilds", _I64), ("pair_contacts", _I64),
                 ("mesh_contacts", _I64), ("list_entries", _I64), ("mesh_candidates", _I64),
                 ("max_list_len", _I32), ("status", _I32), ("launches_per_step", _I32),
-                ("launches_per_rebuild", _I32)]
+                ("launches_per_rebuild", _I32), ("active", _I64), ("capacity", _I64)]
 
 
 class DemError(RuntimeError):
@@ -127,7 +130,9 @@ def _p(a):
 
 def make_params(p: dict, precision: int = DEM_FP64, skin: float = 0.0, max_neighbors: int = 0,
                 max_mesh_contacts: int = 0, record_forces: bool = False,
-                domain=None) -> dem_params:
+                domain=None, spawn=None) -> dem_params:
+    """dem_params from a parameter dict; `spawn` (optional) is a dict with
+    n_max, lo, hi, r_min, r_max, v0, w0, attempts, every, seed (Sec. 3.1)."""
     dp = dem_params()
     for k in ("E", "nu", "rho", "e_n", "mu_s", "mu_r", "mu_t", "eta", "dt"):
         setattr(dp, k, float(p[k]))
@@ -142,6 +147,17 @@ def make_params(p: dict, precision: int = DEM_FP64, skin: float = 0.0, max_neigh
     dp.max_neighbors = int(max_neighbors)
     dp.max_mesh_contacts = int(max_mesh_contacts)
     dp.record_forces = 1 if record_forces else 0
+    if spawn is not None:
+        dp.n_max = int(spawn["n_max"])
+        dp.spawn_lo[:] = [float(c) for c in spawn["lo"]]
+        dp.spawn_hi[:] = [float(c) for c in spawn["hi"]]
+        dp.spawn_r_min = float(spawn["r_min"])
+        dp.spawn_r_max = float(spawn["r_max"])
+        dp.spawn_v0[:] = [float(c) for c in spawn.get("v0", (0.0, 0.0, 0.0))]
+        dp.spawn_w0[:] = [float(c) for c in spawn.get("w0", (0.0, 0.0, 0.0))]
+        dp.spawn_attempts = int(spawn["attempts"])
+        dp.spawn_every = int(spawn.get("every", 1))
+        dp.spawn_seed = int(spawn.get("seed", 0))
     return dp
 
 
@@ -178,21 +194,21 @@ class Scene:
                  tri_radius=None, elems=None, elem_radius=None,
                  precision: int = DEM_FP64, skin: float = 0.0,
                  max_neighbors: int = 0, max_mesh_contacts: int = 0,
-                 record_forces: bool = False, domain=None, stream=None):
+                 record_forces: bool = False, domain=None, stream=None, spawn=None):
         lib = load()
         self._lib = lib
         self._h = ctypes.c_void_p()
         R = _f64(R, (-1,))
         n = R.shape[0]
-        self.n = n
-        self.R = R.copy()
+        # rows: the given particles, then (with spawning) inactive rows up to n_max
+        self.n = max(n, int(spawn["n_max"])) if spawn is not None else n
         x = _f64(x, (n, 3))
         v = None if v is None else _f64(v, (n, 3))
         w = None if w is None else _f64(w, (n, 3))
         q = None if q is None else _f64(q, (n, 4))
         self.precision = precision
         self._pp = make_params(params, precision, skin, max_neighbors, max_mesh_contacts,
-                               record_forces, domain)
+                               record_forces, domain, spawn)
         pa = dem_particles(n, _p(R), _p(x), _p(v), _p(w), _p(q))
         keep = [R, x, v, w, q]
         me = dem_mesh()
@@ -221,9 +237,24 @@ class Scene:
 
     @classmethod
     def from_dict(cls, s: dict, **kw):
+        kw.setdefault("spawn", s.get("spawn"))
         return cls(s["params"], s["R"], s["x"], s.get("v"), s.get("w"), s.get("q"),
                    s.get("verts"), s.get("tris"), s.get("tri_radius"), s.get("elems"),
                    s.get("elem_radius"), **kw)
+
+    @property
+    def R(self) -> np.ndarray:
+        """Radii of all rows (0 for rows awaiting spawning)."""
+        return self.radii()
+
+    def radii(self) -> np.ndarray:
+        R = np.empty(self.n)
+        _check(self._lib.dem_read_radii(self._h, _p(R)), "dem_read_radii")
+        return R
+
+    @property
+    def active(self) -> int:
+        return int(self.stats()["active"])
 
     def close(self):
         if getattr(self, "_h", None) and self._h.value:
