@@ -50,6 +50,10 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=0, help="0: steps // 20")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-ensemble section")
+    ap.add_argument("--batch-scenes", type=int, default=512)
+    ap.add_argument("--batch-steps", type=int, default=500)
+    ap.add_argument("--batch-settle", type=int, default=3000)
     return ap.parse_args()
 
 
@@ -330,6 +334,13 @@ def bench_ours(a):
                       "d2h_bytes_per_step": int(frames * n * (4 * rec + 4) / steps_e2e),
                       "status": rce, "frames": frames, "steps_per_frame": a.frame}
 
+    out["contacts_per_s"] = (st["pair_contacts"] + st["mesh_contacts"]) * a.steps * world / elapsed
+
+    # batched ensemble beside it: independent hopper scenes with per-scene
+    # friction in one scene (one graph replay steps them all), autotuned
+    if not a.no_batch:
+        out["batched"] = bench_batch(a, dem, strm, barrier, rank_max, world)
+
     if rank == 0 and not a.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(target_s=15.0)
     if rank == 0:
@@ -337,6 +348,55 @@ def bench_ours(a):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def bench_batch(a, dem, strm, barrier, rank_max, world):
+    import torch
+    from paper_2507_12610_gb300 import batch
+    b = batch.combine(batch.ensemble(a.batch_scenes))
+    n = len(b["R"])
+    # settle the funnels' lattices into contact (not timed); the settled state
+    # is the input of the tuning runs and of the timed run
+    with torch.cuda.stream(strm):
+        sc = dem.Scene.from_dict(b, precision=dem.DEM_MIXED)
+    sc.step(a.batch_settle)
+    assert sc.synchronize() == 0, "batch settle failed"
+    st = sc.state()
+    sc.close()
+    b = dict(b, x=st["x"], v=st["v"], w=st["w"], q=st["q"])
+    best, table = batch.autotune(b, precision=dem.DEM_MIXED, skins=[0.2e-3, 0.4e-3],
+                                 steps=100, warmup=20, dem=dem)
+    with torch.cuda.stream(strm):
+        sc = dem.Scene.from_dict(b, precision=dem.DEM_MIXED, skin=best["skin"],
+                                 step_warps=best["step_warps"])
+    sc.step(max(3, a.warmup))
+    sc.synchronize()
+    st0 = sc.stats()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    k = a.batch_steps
+    barrier()
+    e0.record(strm)
+    sc.step(k)
+    e1.record(strm)
+    e1.synchronize()
+    rc = sc.synchronize()
+    t = rank_max(e0.elapsed_time(e1) / 1e3)
+    st = sc.stats()
+    f = batch.discharged(b, sc.state()["x"])
+    sc.close()
+    return {"value": aggregate_rate(n, k, t, world), "unit": UNIT, "ms_per_step": t / k * 1e3,
+            "steps": k, "status": rc, "n_scenes": a.batch_scenes, "n_particles": n,
+            "n_triangles": int(len(b["tris"])), "n_rectangles": int(len(b["elems"])),
+            "workload": "hopper discharge, particles log-uniform in [500, 20000] per scene, "
+                        "R~U[0.9,1.1] mm, 256-triangle funnel + 5-rectangle catch box, "
+                        "mu_s~U[0.2,0.8], mu_r~U[0,0.2], mu_t~U[0,0.2] per scene",
+            "precision": "mixed", "settle_steps": a.batch_settle,
+            "autotuned": best, "autotune_table": table,
+            "rebuilds_in_timed": st["rebuilds"] - st0["rebuilds"],
+            "pair_contacts": st["pair_contacts"], "mesh_contacts": st["mesh_contacts"],
+            "contacts_per_s": (st["pair_contacts"] + st["mesh_contacts"]) * k * world / t,
+            "discharged_fraction_median": float(np.median(f))}
 
 
 def oracle_sample():

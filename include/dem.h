@@ -105,6 +105,10 @@ typedef struct dem_params {
   int32_t spawn_attempts;   /* attempts per spawn event, 0 .. 1024 */
   int32_t spawn_every;      /* steps between spawn events; <= 0 selects 1 */
   uint64_t spawn_seed;
+  int32_t step_warps;       /* warps per block of the contact/integration kernel:
+                               4 or 8; <= 0 selects 4 (a tuning knob, results do not
+                               depend on it) */
+  int32_t reserved;
 } dem_params;
 
 /* Particles (host arrays, caller order). */
@@ -115,6 +119,16 @@ typedef struct dem_particles {
   const double* v;   /* [n][3] velocities; NULL = zero */
   const double* w;   /* [n][3] angular velocities; NULL = zero */
   const double* q;   /* [n][4] unit quaternions (scalar first); NULL = identity */
+  /* Friction per material (extension for batched independent scenes; the
+   * paper has one material).  With n_materials > 0 each particle carries the
+   * material material[i] (NULL: 0; spawned particles: 0) whose coefficients
+   * are material_mu[3 m .. 3 m + 2] = mu_s, mu_r, mu_t, replacing those of
+   * dem_params; a particle pair uses the mean of its two materials'
+   * coefficients, a mesh contact the particle's.  n_materials = 0: one
+   * material, the coefficients of dem_params. */
+  int32_t n_materials;        /* 0 .. 65536 */
+  const int32_t* material;    /* [n] material index in [0, n_materials) */
+  const double* material_mu;  /* [n_materials][3], each >= 0 */
 } dem_particles;
 
 /* Rigid mesh in its reference pose (host arrays); may be empty.  Its elements

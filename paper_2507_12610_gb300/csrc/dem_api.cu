@@ -171,6 +171,7 @@ int validate(const dem_params* pr, const dem_particles* pa, const dem_mesh* me) 
   // spawning (Sec. 3.1)
   const bool spawn = pr->spawn_attempts != 0;
   if (pr->spawn_attempts < 0 || pr->spawn_attempts > kSpawnMaxAttempts) return DEM_ERR_INVALID;
+  if (pr->step_warps > 0 && pr->step_warps != 4 && pr->step_warps != 8) return DEM_ERR_INVALID;
   if (pr->n_max > (int64_t)0x7fffffff / 2) return DEM_ERR_INVALID;
   if (spawn) {
     const double sp[] = {pr->spawn_lo[0], pr->spawn_lo[1], pr->spawn_lo[2], pr->spawn_hi[0],
@@ -186,6 +187,16 @@ int validate(const dem_params* pr, const dem_particles* pa, const dem_mesh* me) 
   if (pa->n < (spawn ? 0 : 1) || pa->n > (int64_t)0x7fffffff / 2) return DEM_ERR_INVALID;
   if (pa->n > 0 && (!pa->R || !pa->x)) return DEM_ERR_INVALID;
   const int64_t n = pa->n;
+  if (pa->n_materials < 0 || pa->n_materials > 65536) return DEM_ERR_INVALID;
+  if (pa->n_materials > 0) {
+    if (!pa->material_mu || !finite_all(pa->material_mu, 3 * (int64_t)pa->n_materials))
+      return DEM_ERR_INVALID;
+    for (int64_t k = 0; k < 3 * (int64_t)pa->n_materials; ++k)
+      if (pa->material_mu[k] < 0) return DEM_ERR_INVALID;
+    if (pa->material)
+      for (int64_t i = 0; i < n; ++i)
+        if (pa->material[i] < 0 || pa->material[i] >= pa->n_materials) return DEM_ERR_INVALID;
+  }
   for (int64_t i = 0; i < n; ++i)
     if (!(pa->R[i] > 0) || !std::isfinite(pa->R[i])) return DEM_ERR_INVALID;
   if (!finite_all(pa->x, 3 * n)) return DEM_ERR_INVALID;
@@ -204,6 +215,12 @@ double beta_of(double e_n) {
 }
 
 // Host-side split of a double into the hi/lo pair used by DEM_MIXED.
+inline float int_bits_as_float(int32_t v) {
+  float f;
+  std::memcpy(&f, &v, sizeof f);
+  return f;
+}
+
 inline void split(double a, float& hi, float& lo) {
   hi = (float)a;
   lo = (float)(a - (double)hi);
@@ -479,8 +496,8 @@ int install_contacts(dem_scene* s, const std::vector<ContactRow>& rows, uint32_t
 // Upload a state given in caller order (slot = caller index) into buffer 0,
 // reset the control block to (step, lphase 0), and request a rebuild.
 int upload_state(dem_scene* s, const double* x, const double* v, const double* w,
-                 const double* q, const double* R, int64_t step, int64_t n_active,
-                 double spawn_carry, uint64_t spawn_draws) {
+                 const double* q, const double* R, const int32_t* mat, int64_t step,
+                 int64_t n_active, double spawn_carry, uint64_t spawn_draws) {
   const int64_t n = s->n;
   const double rho = s->p.rho;
   if (s->p.mixed) {
@@ -500,7 +517,7 @@ int upload_state(dem_scene* s, const double* x, const double* v, const double* w
       split(w ? w[3 * i + 1] : 0.0, W[i].hi.y, W[i].lo.y);
       split(w ? w[3 * i + 2] : 0.0, W[i].hi.z, W[i].lo.z);
       W[i].hi.w = R[i] > 0 ? (float)(1.0 / R[i]) : 0.f;  // inverse radius
-      W[i].lo.w = 0.f;
+      W[i].lo.w = int_bits_as_float(mat ? mat[i] : 0);  // material index (int bits)
       split(q ? q[4 * i] : 1.0, Q[i].hi.x, Q[i].lo.x);
       split(q ? q[4 * i + 1] : 0.0, Q[i].hi.y, Q[i].lo.y);
       split(q ? q[4 * i + 2] : 0.0, Q[i].hi.z, Q[i].lo.z);
@@ -516,7 +533,8 @@ int upload_state(dem_scene* s, const double* x, const double* v, const double* w
       const double m = 4.0 / 3.0 * M_PI * rho * R[i] * R[i] * R[i];
       P[i] = make_D4(x[3 * i], x[3 * i + 1], x[3 * i + 2], R[i]);
       V[i] = v ? make_D4(v[3 * i], v[3 * i + 1], v[3 * i + 2], m) : make_D4(0, 0, 0, m);
-      W[i] = w ? make_D4(w[3 * i], w[3 * i + 1], w[3 * i + 2], 0) : make_D4(0, 0, 0, 0);
+      const double mi = mat ? (double)mat[i] : 0.0;  // material index in .w
+      W[i] = w ? make_D4(w[3 * i], w[3 * i + 1], w[3 * i + 2], mi) : make_D4(0, 0, 0, mi);
       Q[i] = q ? make_D4(q[4 * i], q[4 * i + 1], q[4 * i + 2], q[4 * i + 3])
                : make_D4(1, 0, 0, 0);
     }
@@ -654,6 +672,7 @@ int dem_scene_create(const dem_params* params, const dem_particles* parts, const
   p.cap = params->max_neighbors > 0 ? params->max_neighbors : 64;
   p.capm = params->max_mesh_contacts > 0 ? params->max_mesh_contacts : 16;
   s->hist_bytes = p.mixed ? sizeof(HistM) : sizeof(HistD);
+  p.step_warps = params->step_warps == 8 ? 8 : 4;
   p.sp_attempts = spawning ? params->spawn_attempts : 0;
   p.sp_every = params->spawn_every > 0 ? params->spawn_every : 1;
   p.sp_seed = params->spawn_seed;
@@ -856,6 +875,24 @@ int dem_scene_create(const dem_params* params, const dem_particles* parts, const
     s->mesh.curl = M.get<float4>(4 * (size_t)s->nt);
     s->mesh.plane = M.get<float4>(2 * (size_t)s->nt);
   }
+  if (parts->n_materials > 0) {
+    p.n_mat = parts->n_materials;
+    float4* mf = M.get<float4>(p.n_mat);
+    D4* md = M.get<D4>(p.n_mat);
+    if (M.failed) return fail(DEM_ERR_NOMEM);
+    std::vector<float4> hf(p.n_mat);
+    std::vector<D4> hd(p.n_mat);
+    for (int k = 0; k < p.n_mat; ++k) {
+      const double* m = parts->material_mu + 3 * (size_t)k;
+      hf[k] = make_float4((float)m[0], (float)m[1], (float)m[2], 0.f);
+      hd[k] = make_D4(m[0], m[1], m[2], 0.0);
+    }
+    if (cudaMemcpy(mf, hf.data(), p.n_mat * sizeof(float4), cudaMemcpyHostToDevice) ||
+        cudaMemcpy(md, hd.data(), p.n_mat * sizeof(D4), cudaMemcpyHostToDevice))
+      return fail(DEM_ERR_CUDA);
+    p.mat_f = mf;
+    p.mat_d = md;
+  }
   if (M.failed) return fail(DEM_ERR_NOMEM);
   s->mesh.nv = s->nv;
   s->mesh.nt = s->nt;
@@ -886,7 +923,11 @@ int dem_scene_create(const dem_params* params, const dem_particles* parts, const
       if (parts->q)
         for (int a = 0; a < 4; ++a) q[4 * i + a] = parts->q[4 * i + a];
     }
-    rc = upload_state(s, x.data(), v.data(), w.data(), q.data(), R.data(), 0, n_init, -1.0, 0);
+    std::vector<int32_t> mat(n, 0);
+    if (parts->material && parts->n_materials > 0)
+      for (int64_t i = 0; i < n_init; ++i) mat[i] = parts->material[i];
+    rc = upload_state(s, x.data(), v.data(), w.data(), q.data(), R.data(), mat.data(), 0,
+                      n_init, -1.0, 0);
   }
   if (rc != DEM_OK) return fail(rc);
   // pose at step 0 (a static mesh keeps it)

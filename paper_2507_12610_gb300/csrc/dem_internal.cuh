@@ -82,6 +82,12 @@ struct Params {
   uint64_t sp_seed;
   int32_t sp_attempts;      // 0: spawning off
   int32_t sp_every;
+  // friction per material (n_mat = 0: the coefficients above); the material
+  // index of a particle is in its W record (mixed: lo.w as int bits; FP64: w)
+  int32_t step_warps;       // warps per block of the step kernel (4 or 8)
+  int32_t n_mat;
+  const float4* mat_f;      // [n_mat] mu_s, mu_r, mu_t, 0
+  const D4* mat_d;          // [n_mat] mu_s, mu_r, mu_t, 0
 };
 
 constexpr int kSpawnMaxAttempts = 1024;

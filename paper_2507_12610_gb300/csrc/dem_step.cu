@@ -304,8 +304,13 @@ struct MixedPolicy {
                                               float c6[6]) {
     Geo g;
     if (!touch(p, Pi, Pj, g)) return false;
-    const LawConst<float> cpp{p.f_Es_pp, p.f_Gs_pp, p.f_beta, p.f_mu_s, p.f_mu_r, p.f_mu_t,
-                              p.f_dt};
+    LawConst<float> cpp{p.f_Es_pp, p.f_Gs_pp, p.f_beta, p.f_mu_s, p.f_mu_r, p.f_mu_t, p.f_dt};
+    if (p.n_mat > 0) {  // the mean of the two materials' coefficients
+      const float4 a = p.mat_f[__float_as_int(Wi.lo.w)], b = p.mat_f[__float_as_int(Wj.lo.w)];
+      cpp.mu_s = (a.x + b.x) * 0.5f;
+      cpp.mu_r = (a.y + b.y) * 0.5f;
+      cpp.mu_t = (a.z + b.z) * 0.5f;
+    }
     const float Ri = Pi.hi.w + Pi.lo.w, Rj = Pj.hi.w + Pj.lo.w;
     const float Rs = 1.f / (Wi.hi.w + Wj.hi.w);  // records carry 1/R and 1/m
     const float ms = 1.f / (Vi.lo.w + Vj.lo.w);
@@ -361,8 +366,14 @@ struct MixedPolicy {
     // pick the nearest feature, then the overlap of the near candidates in
     // compensated FP32 (an element is large compared with the overlap)
     if (ntc > 0) {
-      const LawConst<float> cpw{p.f_Es_pw, p.f_Gs_pw, p.f_beta, p.f_mu_s, p.f_mu_r, p.f_mu_t,
-                                p.f_dt};
+      LawConst<float> cpw{p.f_Es_pw, p.f_Gs_pw, p.f_beta, p.f_mu_s, p.f_mu_r, p.f_mu_t,
+                          p.f_dt};
+      if (p.n_mat > 0) {  // the particle's material
+        const float4 a = p.mat_f[__float_as_int(Wt.lo.w)];
+        cpw.mu_s = a.x;
+        cpw.mu_r = a.y;
+        cpw.mu_t = a.z;
+      }
       HistM* hpm = static_cast<HistM*>(lb.hpm);
       const V3<float> qf = sum3(Pt);
       const V3<float> Om = mk(p.f_omega[0], p.f_omega[1], p.f_omega[2]);
@@ -502,8 +513,7 @@ void launch_mesh_pose(cudaStream_t st, const Ctl* ctl, const Params& p, MeshDev 
 void launch_step(cudaStream_t st, Ctl* ctl, const Params& p, StateBufs sb, Lists L,
                  MeshDev mesh, double* forces) {
   if (p.mixed)
-    k_step_warp<MixedPolicy><<<(unsigned)((p.n + kStepThreads - 1) / kStepThreads), kStepThreads,
-                               0, st>>>(ctl, p, sb, L, mesh, forces);
+    launch_step_warp<MixedPolicy>(st, ctl, p, sb, L, mesh, forces);
   else
     launch_step_fp64(st, ctl, p, sb, L, mesh, forces);
 }

@@ -75,7 +75,13 @@ struct Fp64Policy {
                                               double c6[6]) {
     Geo g;
     if (!touch(p, Pi, Pj, g)) return false;
-    const LawConst<double> cpp{p.Es_pp, p.Gs_pp, p.beta, p.mu_s, p.mu_r, p.mu_t, p.dt};
+    LawConst<double> cpp{p.Es_pp, p.Gs_pp, p.beta, p.mu_s, p.mu_r, p.mu_t, p.dt};
+    if (p.n_mat > 0) {  // the mean of the two materials' coefficients
+      const D4 a = p.mat_d[(int)Wi.w], b = p.mat_d[(int)Wj.w];
+      cpp.mu_s = (a.x + b.x) * 0.5;
+      cpp.mu_r = (a.y + b.y) * 0.5;
+      cpp.mu_t = (a.z + b.z) * 0.5;
+    }
     const V3<double> nh = (1.0 / g.dist) * g.d;
     const double Ri = Pi.w, Rj = Pj.w;
     const double Rs = 1.0 / (1.0 / Ri + 1.0 / Rj);
@@ -130,6 +136,12 @@ struct Fp64Policy {
     // particle-triangle contacts
     if (ntc > 0) {
       LawConst<double> cpw{p.Es_pw, p.Gs_pw, p.beta, p.mu_s, p.mu_r, p.mu_t, p.dt};
+      if (p.n_mat > 0) {  // the particle's material
+        const D4 a = p.mat_d[(int)Wt.w];
+        cpw.mu_s = a.x;
+        cpw.mu_r = a.y;
+        cpw.mu_t = a.z;
+      }
       HistD* hpm = static_cast<HistD*>(lb.hpm);
       const V3<double> x = xyz(Pt);
       const V3<double> Om = mk(p.mesh_omega[0], p.mesh_omega[1], p.mesh_omega[2]);
@@ -210,7 +222,7 @@ struct Fp64Policy {
     D4* Qn = static_cast<D4*>(buf_of(sb.Q, ph ^ 1u));
     Pn[t] = make_D4(x.x, x.y, x.z, R);
     Vn[t] = make_D4(v.x, v.y, v.z, mass);
-    Wn[t] = make_D4(w.x, w.y, w.z, 0.0);
+    Wn[t] = make_D4(w.x, w.y, w.z, Wt.w);  // .w: material index
     Qn[t] = make_D4(q[0], q[1], q[2], q[3]);
     if (p.record_forces) {
       double* fo = forces + 6 * (size_t)t;
@@ -229,8 +241,7 @@ struct Fp64Policy {
 
 void launch_step_fp64(cudaStream_t st, Ctl* ctl, const Params& p, StateBufs sb, Lists L,
                       MeshDev mesh, double* forces) {
-  k_step_warp<Fp64Policy><<<(unsigned)((p.n + kStepThreads - 1) / kStepThreads), kStepThreads, 0,
-                            st>>>(ctl, p, sb, L, mesh, forces);
+  launch_step_warp<Fp64Policy>(st, ctl, p, sb, L, mesh, forces);
 }
 
 }  // namespace dem

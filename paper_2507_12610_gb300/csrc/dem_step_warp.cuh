@@ -26,8 +26,9 @@
 
 namespace dem {
 
-constexpr int kStepWarps = 4;             // warps per block
-constexpr int kStepThreads = 32 * kStepWarps;
+// Warps per block: 4 by default; 8 is the other shape the autotuner can pick
+// (dem_params.step_warps).  The resident-block bound of a policy is stated
+// for 4-warp blocks and scaled for others, so the threads per SM stay alike.
 constexpr int kQueueMax = 512;            // queued contacts per warp and round
 
 template <typename CT>
@@ -51,19 +52,19 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
   return v;
 }
 
-template <typename Pol>
-__global__ void __launch_bounds__(kStepThreads, Pol::kMinBlocks)
+template <typename Pol, int Warps>
+__global__ void __launch_bounds__(32 * Warps, (Pol::kMinBlocks * 4 / Warps > 0 ? Pol::kMinBlocks * 4 / Warps : 1))
 k_step_warp(Ctl* ctl, Params p, StateBufs sb, Lists L, MeshDev mesh, double* forces) {
   using Rec = typename Pol::Rec;
   using Hist = typename Pol::Hist;
   using CT = typename Pol::T;
-  __shared__ WarpScratch<CT> smem[kStepWarps];
+  __shared__ WarpScratch<CT> smem[Warps];
   if (ctl->status) return;
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   WarpScratch<CT>& S = smem[wib];
   const int n = p.n;
-  const int w0 = (blockIdx.x * kStepWarps + wib) * 32;
+  const int w0 = (blockIdx.x * Warps + wib) * 32;
   const int t = w0 + lane;
   const bool valid = t < n;
   const uint32_t ph = ctl->phase & 1u, lph = ctl->lphase & 1u;
@@ -174,6 +175,17 @@ k_step_warp(Ctl* ctl, Params p, StateBufs sb, Lists L, MeshDev mesh, double* for
                 W[t], acc, stamp_now, stamp_new, forces, nmesh, disp, bad);
 
   count_and_flag(ctl, npair, nmesh, disp, bad);
+}
+
+template <typename Pol>
+void launch_step_warp(cudaStream_t st, Ctl* ctl, const Params& p, StateBufs sb, Lists L,
+                      MeshDev mesh, double* forces) {
+  if (p.step_warps == 8)
+    k_step_warp<Pol, 8><<<(unsigned)((p.n + 255) / 256), 256, 0, st>>>(ctl, p, sb, L, mesh,
+                                                                        forces);
+  else
+    k_step_warp<Pol, 4><<<(unsigned)((p.n + 127) / 128), 128, 0, st>>>(ctl, p, sb, L, mesh,
+                                                                        forces);
 }
 
 }  // namespace dem

@@ -48,11 +48,14 @@ class dem_params(ctypes.Structure):
                 ("record_forces", _I32), ("n_max", _I64), ("spawn_lo", _D * 3),
                 ("spawn_hi", _D * 3), ("spawn_r_min", _D), ("spawn_r_max", _D),
                 ("spawn_v0", _D * 3), ("spawn_w0", _D * 3), ("spawn_attempts", _I32),
-                ("spawn_every", _I32), ("spawn_seed", ctypes.c_uint64)]
+                ("spawn_every", _I32), ("spawn_seed", ctypes.c_uint64),
+                ("step_warps", _I32), ("reserved", _I32)]
 
 
 class dem_particles(ctypes.Structure):
-    _fields_ = [("n", _I64), ("R", _DP), ("x", _DP), ("v", _DP), ("w", _DP), ("q", _DP)]
+    _fields_ = [("n", _I64), ("R", _DP), ("x", _DP), ("v", _DP), ("w", _DP), ("q", _DP),
+                ("n_materials", _I32), ("material", ctypes.POINTER(ctypes.c_int32)),
+                ("material_mu", _DP)]
 
 
 class dem_mesh(ctypes.Structure):
@@ -130,7 +133,7 @@ def _p(a):
 
 def make_params(p: dict, precision: int = DEM_FP64, skin: float = 0.0, max_neighbors: int = 0,
                 max_mesh_contacts: int = 0, record_forces: bool = False,
-                domain=None, spawn=None) -> dem_params:
+                domain=None, spawn=None, step_warps: int = 0) -> dem_params:
     """dem_params from a parameter dict; `spawn` (optional) is a dict with
     n_max, lo, hi, r_min, r_max, v0, w0, attempts, every, seed (Sec. 3.1)."""
     dp = dem_params()
@@ -147,6 +150,7 @@ def make_params(p: dict, precision: int = DEM_FP64, skin: float = 0.0, max_neigh
     dp.max_neighbors = int(max_neighbors)
     dp.max_mesh_contacts = int(max_mesh_contacts)
     dp.record_forces = 1 if record_forces else 0
+    dp.step_warps = int(step_warps)
     if spawn is not None:
         dp.n_max = int(spawn["n_max"])
         dp.spawn_lo[:] = [float(c) for c in spawn["lo"]]
@@ -194,7 +198,8 @@ class Scene:
                  tri_radius=None, elems=None, elem_radius=None,
                  precision: int = DEM_FP64, skin: float = 0.0,
                  max_neighbors: int = 0, max_mesh_contacts: int = 0,
-                 record_forces: bool = False, domain=None, stream=None, spawn=None):
+                 record_forces: bool = False, domain=None, stream=None, spawn=None,
+                 material=None, material_mu=None, step_warps: int = 0):
         lib = load()
         self._lib = lib
         self._h = ctypes.c_void_p()
@@ -208,9 +213,19 @@ class Scene:
         q = None if q is None else _f64(q, (n, 4))
         self.precision = precision
         self._pp = make_params(params, precision, skin, max_neighbors, max_mesh_contacts,
-                               record_forces, domain, spawn)
+                               record_forces, domain, spawn, step_warps)
         pa = dem_particles(n, _p(R), _p(x), _p(v), _p(w), _p(q))
         keep = [R, x, v, w, q]
+        if material_mu is not None:
+            # friction per material: (n_mat, 3) mu_s, mu_r, mu_t; material[i] per particle
+            mu = _f64(material_mu, (-1, 3))
+            mat = None if material is None else np.ascontiguousarray(
+                np.asarray(material, dtype=np.int32).reshape(n))
+            pa.n_materials = mu.shape[0]
+            pa.material_mu = _p(mu)
+            if mat is not None:
+                pa.material = mat.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+            keep += [mu, mat]
         me = dem_mesh()
         has_tris = tris is not None and len(tris) > 0
         has_elems = elems is not None and len(elems) > 0
@@ -238,6 +253,8 @@ class Scene:
     @classmethod
     def from_dict(cls, s: dict, **kw):
         kw.setdefault("spawn", s.get("spawn"))
+        kw.setdefault("material", s.get("material"))
+        kw.setdefault("material_mu", s.get("material_mu"))
         return cls(s["params"], s["R"], s["x"], s.get("v"), s.get("w"), s.get("q"),
                    s.get("verts"), s.get("tris"), s.get("tri_radius"), s.get("elems"),
                    s.get("elem_radius"), **kw)

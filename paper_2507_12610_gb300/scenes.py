@@ -362,73 +362,49 @@ def _box_rect(x0, x1, y0, y1, z0, z1):
     return [(x0, y0, z0), (x1, y0, z0), (x1, y1, z0), (x0, y1, z0)]
 
 
-def repose_scene(n=20_000, seed=7, R=1.0e-3, gap_diameters=11, orifice_diameters=10,
-                 mu_s=3.0, mu_r=3.0, speed=0.01, **over):
-    """Quasi-2D heap between two vertical plates (the angle-of-repose example, Sec. 5).
+def repose_scene(n=20_000, seed=7, R=1.0e-3, gap_diameters=11, stream_diameters=6,
+                 mu_s=3.0, mu_r=3.0, attempts=64, every=10, v0=-0.5, **over):
+    """Quasi-2D heap between two vertical plates (the piling example, Sec. 5).
 
-    Monodisperse grains of radius R between plates 11 diameters apart (y), with
-    the material defaults of Table 2 (rho 1000, E 1 MPa, nu 0.3, e_n 0.5), the
-    strong friction mu_s = mu_r = 3, mu_t = 2 mu_s / 3 (Table 2's default rule),
-    and a time step ten times below Eq. dt.  The paper pours a spawned stream;
-    here the grains start on a lattice in a flat-bottomed bin above the middle
-    of the floor and drain through a central orifice (orifice_diameters wide),
-    which also makes a narrow stream.  The bin bottom sits above the height of
-    the final heap for angles up to 60 degrees, the floor and the end walls
-    well outside its base.  All elements are rectangles of radius 0.
+    Monodisperse grains of radius R between plates gap_diameters diameters
+    apart (y), with the material defaults of Table 2 (rho 1000, E 1 MPa, nu 0.3,
+    e_n 0.5), the strong friction mu_s = mu_r = 3, mu_t = 2 mu_s / 3 (Table 2's
+    default rule), and a time step ten times below Eq. dt.  As in the paper, a
+    stream of spawned grains piles up: the spawn box spans the gap, is
+    stream_diameters wide in x and sits above the height of the final heap for
+    angles up to 60 degrees; it gets `attempts` attempts every `every` steps,
+    the grains start with vertical velocity v0, until n grains are in.  The
+    floor and the two end walls are far outside the heap's base.  All mesh
+    elements are rectangles of radius 0.
     """
-    rng = np.random.default_rng(seed)
     d = 2.0 * R
     W = gap_diameters * d
-    pitch = 1.02 * d
-    ny = int(math.floor((W - d) / pitch)) + 1           # grains across the gap
-    # heap size for the solid volume at packing 0.6 (2D triangle of angle theta)
-    area = n * (math.pi / 6.0) * d ** 3 / (0.6 * W)
+    hy = 0.5 * W
+    area = n * (math.pi / 6.0) * d ** 3 / (0.6 * W)  # heap cross-section at packing 0.6
     h60 = math.sqrt(area * math.tan(math.radians(60.0)))
     base40 = 2.0 * math.sqrt(area * math.tan(math.radians(40.0))) / math.tan(math.radians(40.0))
     half_floor = 0.8 * base40 + 5 * d
-    z0 = 1.15 * h60 + 10 * d                               # bin bottom
-    # bin: as wide as 60 lattice columns or a square-ish fill, whichever is larger
-    n_layers_xy = int(math.ceil(n / ny))
-    nx = max(20, int(math.ceil(math.sqrt(n_layers_xy / 2.0))))
-    nz = int(math.ceil(n_layers_xy / nx))
-    half_bin = 0.5 * nx * pitch + 0.5 * d
-    a = 0.5 * orifice_diameters * d
-    if a >= half_bin:
-        raise ValueError("orifice wider than the bin")
-    gi = np.stack(np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij"),
-                  axis=-1).reshape(-1, 3).astype(np.float64)
-    order = np.lexsort((gi[:, 0], gi[:, 1], gi[:, 2]))
-    gi = gi[order][:n]
-    X = np.empty((n, 3))
-    X[:, 0] = (gi[:, 0] - 0.5 * (nx - 1)) * pitch
-    X[:, 1] = (gi[:, 1] - 0.5 * (ny - 1)) * pitch
-    X[:, 2] = z0 + R + 0.01 * d + gi[:, 2] * pitch
-    X += rng.uniform(-0.005 * d, 0.005 * d, size=X.shape)
-    Rv = np.full(n, R)
-    v = rng.normal(scale=speed, size=(n, 3))
-    w = np.zeros((n, 3))
-    q = _unit_quaternions(rng, n)
-    top = z0 + (nz + 2) * pitch
-    hy = 0.5 * W
+    z_sp = 1.1 * h60 + 8 * d
+    top = z_sp + 8 * d
     rects = [
         _box_rect(-half_floor, half_floor, -hy, hy, 0.0, 0.0),            # floor
         _box_rect(-half_floor, half_floor, -hy, -hy, 0.0, top),           # plate y-
         _box_rect(-half_floor, half_floor, hy, hy, 0.0, top),             # plate y+
         _box_rect(-half_floor, -half_floor, -hy, hy, 0.0, h60 + 4 * d),   # end wall x-
         _box_rect(half_floor, half_floor, -hy, hy, 0.0, h60 + 4 * d),     # end wall x+
-        _box_rect(-half_bin, -half_bin, -hy, hy, z0, top),                # bin wall x-
-        _box_rect(half_bin, half_bin, -hy, hy, z0, top),                  # bin wall x+
-        _box_rect(-half_bin, -a, -hy, hy, z0, z0),                        # bin bottom left
-        _box_rect(a, half_bin, -hy, hy, z0, z0),                          # bin bottom right
     ]
     V = np.array([p for r in rects for p in r], dtype=np.float64)
     E = np.arange(4 * len(rects), dtype=np.int32).reshape(-1, 4)
     params = base_params(rho=1000.0, E=1.0e6, nu=0.3, e_n=0.5, mu_s=mu_s, mu_r=mu_r,
                          mu_t=2.0 * mu_s / 3.0, dt=eq_dt(R, 1000.0, 0.3, 1.0e6) / 10.0)
     params.update(over)
+    half_stream = 0.5 * stream_diameters * d
+    spawn = dict(n_max=n, lo=(-half_stream, -hy + R, z_sp), hi=(half_stream, hy - R, z_sp + 4 * d),
+                 r_min=R, r_max=R, v0=(0.0, 0.0, v0), w0=(0.0, 0.0, 0.0), attempts=attempts,
+                 every=every, seed=seed)
     lo = np.array([-half_floor, -hy, 0.0]) - 2 * d
     hi = np.array([half_floor, hy, top]) + 2 * d
-    s = _scene("repose", seed, params, Rv, X, v, w, q, V, None, None, (lo, hi), elems=E,
-               elem_radius=np.zeros(len(E)))
-    s.update(gap=W, z_bin=z0, half_floor=half_floor, h60=h60)
+    s = _scene("repose", seed, params, np.zeros(0), np.zeros((0, 3)), None, None, None, V, None,
+               None, (lo, hi), elems=E, elem_radius=np.zeros(len(E)))
+    s.update(gap=W, half_floor=half_floor, h60=h60, spawn=spawn, z_spawn=z_sp)
     return s

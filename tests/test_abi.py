@@ -51,8 +51,8 @@ def test_struct_layouts_match_header():
     # sizes of the ctypes mirrors against the C layout (all fields naturally aligned)
     from paper_2507_12610_gb300 import dem
     assert ctypes.sizeof(dem.dem_params) == (8 * (8 + 3 + 1 + 3 + 3 + 1 + 3 + 3) + 4 * 4
-                                             + 8 + 8 * (3 + 3 + 2 + 3 + 3) + 4 + 4 + 8)
-    assert ctypes.sizeof(dem.dem_particles) == 8 * 6
+                                             + 8 + 8 * (3 + 3 + 2 + 3 + 3) + 4 + 4 + 8 + 4 + 4)
+    assert ctypes.sizeof(dem.dem_particles) == 8 * 6 + 8 + 8 + 8
     assert ctypes.sizeof(dem.dem_mesh) == 8 * 8
     assert ctypes.sizeof(dem.dem_stats) == 8 * 6 + 4 * 4 + 8 * 2
 

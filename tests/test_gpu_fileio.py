@@ -42,4 +42,8 @@ def test_scene_from_files_matches_arrays(dem, tmp_path, precision):
     last = fileio.read_csv(paths[-1])
     st = b.state()
     assert np.array_equal(last["x"], st["x"]) and np.array_equal(last["q"], st["q"])
-    assert np.array_equal(last["R"], s["R"])
+    # DEM_MIXED keeps radii as two floats (48 significant bits)
+    if precision == 0:
+        assert np.array_equal(last["R"], s["R"])
+    else:
+        assert np.allclose(last["R"], s["R"], rtol=1e-14, atol=0)
