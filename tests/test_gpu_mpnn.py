@@ -1,0 +1,114 @@
+"""The surrogate's kernels (GPU) against numpy and the FP64 network oracle."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sg():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2507_12610_gb300 import build
+    build.build()
+    from paper_2507_12610_gb300 import surrogate
+    surrogate.load()
+    return surrogate
+
+
+def bf16(a):
+    """Round to bfloat16 (nearest even), returned as float32 values and bits."""
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16).astype(np.uint16)
+    return (r.astype(np.uint32) << 16).view(np.float32), r.view(np.int16)
+
+
+def test_gemm_matches_numpy(sg):
+    import torch
+    rng = np.random.default_rng(0)
+    for M, N, K in ((64, 64, 16), (192, 128, 400), (256, 64, 144)):
+        A, Ab = bf16(rng.normal(size=(M, K)))
+        B, Bb = bf16(rng.normal(size=(K, N)))
+        ref = A.astype(np.float64) @ B.astype(np.float64)
+        dA = torch.as_tensor(Ab, device="cuda")
+        dBt = torch.as_tensor(np.ascontiguousarray(Bb.reshape(K, N).T), device="cuda")
+        C = torch.empty((M, N), dtype=torch.float32, device="cuda")
+        sg._call("mpnn_gemm", M, N, K, dA, dBt, C, None, None, sg._i32(0), sg._i32(0), None)
+        got = C.cpu().numpy()
+        assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref).max(), (M, N, K)
+        # split along k: the same up to the order of the partial sums
+        work = torch.empty((4, M, N), dtype=torch.float32, device="cuda")
+        C2 = torch.empty_like(C)
+        sg._call("mpnn_gemm_split", M, N, K, sg._i32(4), dA, dBt, C2, sg._i32(0), work, None)
+        assert np.abs(C2.cpu().numpy() - ref).max() <= 1e-5 * np.abs(ref).max()
+
+
+def test_graph_is_all_pairs_within_cutoff(sg):
+    mo = pytest.importorskip("oracle.mpnn_oracle")
+    rng = np.random.default_rng(1)
+    x = rng.uniform(0, 0.02, size=(700, 3))
+    R = np.full(700, 1e-3)
+    g = sg.Graph(x, np.zeros_like(x), np.zeros_like(x), R, 2.2e-3, 0.1, 1e-3)
+    off, nbr, dst = g.edges_host()
+    off_r, nbr_r = mo.neighbours(x.astype(np.float32).astype(np.float64), 2.2e-3)
+    assert np.array_equal(off, off_r) and np.array_equal(nbr, nbr_r)
+    assert np.array_equal(dst, np.repeat(np.arange(700), np.diff(off)))
+    perm = g.perm[:g.E].cpu().numpy()
+    # perm lists, per sender, the edges it sends: their sender is that node
+    send = np.repeat(np.arange(700), np.diff(off))
+    assert np.array_equal(nbr[perm], send) and np.array_equal(np.sort(perm), np.arange(g.E))
+
+
+def small_state(n=400, seed=2):
+    rng = np.random.default_rng(seed)
+    side = int(round(n ** (1 / 3))) + 1
+    gi = np.stack(np.meshgrid(*[np.arange(side)] * 3, indexing="ij"), -1).reshape(-1, 3)[:n]
+    x = gi * 2.05e-3 + rng.uniform(-1e-4, 1e-4, size=(n, 3))
+    return dict(x=x, v=rng.normal(scale=0.05, size=(n, 3)), w=rng.normal(scale=30, size=(n, 3)),
+                R=rng.uniform(0.9e-3, 1.1e-3, n))
+
+
+def test_forward_and_gradients_match_the_fp64_network(sg):
+    mo = pytest.importorskip("oracle.mpnn_oracle")
+    s = small_state()
+    R = s["R"]
+    model = sg.MPNN(seed=3)
+    g = sg.make_graph(s["x"], s["v"], s["w"], R, R.max())
+    rng = np.random.default_rng(4)
+    T = rng.normal(scale=0.3, size=(g.n, 6))
+    loss = model.loss_and_grad(g, sg.target_buffer(T, g.npad))
+    # the oracle on the same (bf16-rounded) weights and the same graph
+    W = {k: bf16(v)[0].astype(np.float64) for k, v in model.weights().items()}
+    off, nbr, dst = g.edges_host()
+    nf, ef, dst_r = mo.features(s["x"], s["v"], s["w"], R, off, nbr, sg.SCALES["vs"],
+                                sg.SCALES["Rs"])
+    assert np.array_equal(dst, dst_r)
+    loss_r, y_r, G_r = mo.loss_and_grads(W, nf, ef, dst_r, nbr, T)
+    y = model.forward(g)[:g.n, :6].cpu().numpy()
+    assert np.abs(y - y_r).max() <= 3e-2 * np.abs(y_r).max()
+    assert loss == pytest.approx(loss_r, rel=3e-2)
+    for name in sg.LAYERS:
+        kin = sg.LAYERS[name][0]
+        gg = model.G[name][:kin].cpu().numpy()
+        gr = G_r[name]
+        err = np.linalg.norm(gg - gr) / np.linalg.norm(gr)
+        assert err < 6e-2, (name, err)
+
+
+def test_training_reduces_the_loss(sg):
+    s = small_state(n=600, seed=5)
+    R = s["R"]
+    model = sg.MPNN(seed=6)
+    g = sg.make_graph(s["x"], s["v"], s["w"], R, R.max())
+    rng = np.random.default_rng(7)
+    # a smooth target the network can represent: a function of the velocity
+    T = np.tanh(3 * s["v"] / 0.1) * 0.5
+    T = np.hstack([T, -T])
+    buf = sg.target_buffer(T, g.npad)
+    first = model.loss_and_grad(g, buf)
+    for _ in range(60):
+        model.loss_and_grad(g, buf)
+        model.adam(2e-3)
+    last = model.loss_and_grad(g, buf)
+    assert last < 0.2 * first, (first, last)
