@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--batch-scenes", type=int, default=512)
     ap.add_argument("--batch-steps", type=int, default=500)
     ap.add_argument("--batch-settle", type=int, default=3000)
+    ap.add_argument("--no-surrogate", action="store_true")
     return ap.parse_args()
 
 
@@ -341,6 +342,11 @@ def bench_ours(a):
     if not a.no_batch:
         out["batched"] = bench_batch(a, dem, strm, barrier, rank_max, world)
 
+    # the learned surrogate beside it: graph + network per stride of 10 steps
+    # on a 100k drum, against 10 DEM steps on the same drum
+    if not a.no_surrogate:
+        out["surrogate"] = bench_surrogate(dem, strm)
+
     if rank == 0 and not a.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(target_s=15.0)
     if rank == 0:
@@ -397,6 +403,37 @@ def bench_batch(a, dem, strm, barrier, rank_max, world):
             "pair_contacts": st["pair_contacts"], "mesh_contacts": st["mesh_contacts"],
             "contacts_per_s": (st["pair_contacts"] + st["mesh_contacts"]) * k * world / t,
             "discharged_fraction_median": float(np.median(f))}
+
+
+def bench_surrogate(dem, strm, n=100_000):
+    import torch
+    from paper_2507_12610_gb300 import scenes, surrogate
+    d = scenes.drum_scene(n=n, seed=5, nn_dist=2.15e-3, speed=0.02,
+                          radius=scenes.drum_geometry(n)[0])
+    with torch.cuda.stream(strm):
+        sc = dem.Scene.from_dict(d, precision=dem.DEM_MIXED)
+    sc.step(500)
+    st = sc.state()
+    sc.synchronize()
+    t0 = time.perf_counter()
+    sc.step(100)
+    sc.synchronize()
+    dem_ms = (time.perf_counter() - t0) * 1e3 / 10
+    sc.close()
+    model = surrogate.MPNN(seed=0)
+    surrogate.predict(model, st, d["R"])  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    k = 3
+    for _ in range(k):
+        surrogate.predict(model, st, d["R"])
+    torch.cuda.synchronize()
+    net_ms = (time.perf_counter() - t0) * 1e3 / k
+    return {"value": n * 10 / (net_ms * 1e-3), "unit": UNIT, "n_particles": n,
+            "stride_steps": 10, "ms_per_stride": net_ms, "dem_ms_per_stride": dem_ms,
+            "gain": dem_ms / net_ms,
+            "note": "network time (all-pairs graph + 3-round MPNN, bf16) per 10-step stride; "
+                    "its trajectory error is measured by paper_2507_12610_gb300.surrogate"}
 
 
 def oracle_sample():

@@ -339,9 +339,10 @@ def sample_pairs(scene, n_samples, every=50, stride=10, settle=2000, precision=1
     return out, R
 
 
-def train(model: MPNN, pairs, R, dt, stride=10, iters=300, lr=1e-3, log_every=50):
+def train(model: MPNN, pairs, R, dt, stride=10, iters=300, lr=1e-3, log_every=50, lr_end=None):
     """Adam on the mean-squared error of the scaled mean accelerations,
-    cycling through the sample pairs; returns the loss history."""
+    cycling through the sample pairs (learning rate decaying geometrically to
+    lr_end if given); returns the loss history."""
     rmax = float(R.max())
     graphs = []
     for a, b in pairs:
@@ -352,7 +353,8 @@ def train(model: MPNN, pairs, R, dt, stride=10, iters=300, lr=1e-3, log_every=50
     for it in range(iters):
         g, T = graphs[it % len(graphs)]
         loss = model.loss_and_grad(g, T)
-        model.adam(lr)
+        rate = lr if lr_end is None else lr * (lr_end / lr) ** (it / max(1, iters - 1))
+        model.adam(rate)
         if it % log_every == 0 or it == iters - 1:
             hist.append((it, loss))
     return hist
@@ -397,3 +399,127 @@ def max_overlap(x, R, rmax):
         return 0.0
     d = np.linalg.norm(x[nbr] - x[dst], axis=1)
     return float(np.max((R[nbr] + R[dst] - d) / np.minimum(R[nbr], R[dst])))
+
+
+def rollout(model: MPNN, state, R, params, strides, stride=10, overlap_growth=0.02,
+            energy_limit=0.5, precision=1):
+    """Hybrid run: each stride, the network's accelerations advance the state
+    unless the largest overlap grows by more than overlap_growth R_min or the
+    kinetic energy changes by more than energy_limit (relative); then the DEM
+    takes that stride from the state before it.  Also runs the DEM alone
+    alongside and returns the per-stride position error of the hybrid
+    (RMS / R_max)."""
+    import time
+    dt = params["dt"]
+    rmax = float(R.max())
+    rho = params["rho"]
+    m = 4.0 / 3.0 * math.pi * rho * R ** 3
+
+    def ke(s):
+        return 0.5 * float(np.sum(m * np.einsum("ij,ij->i", s["v"], s["v"])))
+
+    def dem_stride(s):
+        sc = _dem.Scene(params, R, s["x"], s["v"], s["w"], s["q"], precision=precision,
+                        **_mesh_kw)
+        sc.step(stride)
+        out = sc.state()
+        sc.close()
+        return out
+
+    ref = dict(state)
+    cur = dict(state)
+    rows = []
+    t_net = t_dem = 0.0
+    falls = 0
+    for k in range(strides):
+        t0 = time.perf_counter()
+        acc = predict(model, cur, R)
+        nxt = advance(cur, acc, R, dt, stride)
+        ov0 = max_overlap(cur["x"], R, rmax)
+        ov = max_overlap(nxt["x"], R, rmax)
+        e0, e1 = ke(cur), ke(nxt)
+        t_net += time.perf_counter() - t0
+        if ov > ov0 + overlap_growth or abs(e1 - e0) > energy_limit * max(e0, 1e-30):
+            t0 = time.perf_counter()
+            nxt = dem_stride(cur)
+            t_dem += time.perf_counter() - t0
+            falls += 1
+        cur = nxt
+        ref = dem_stride(ref)
+        err = float(np.sqrt(np.mean(np.sum((cur["x"] - ref["x"]) ** 2, axis=1)))) / rmax
+        rows.append((k + 1, err, ov))
+    return {"strides": strides, "fallbacks": falls, "pos_error_rms_over_rmax": rows,
+            "net_s": t_net, "dem_fallback_s": t_dem}
+
+
+_mesh_kw = {}
+
+
+def experiment(n_scenes=8, n_train=40, n_eval=8, iters=3000, lr=1e-3, drum_n=20_000,
+               strides=10, seed=0):
+    """Train on hopper-discharge trajectories (the batched workload), evaluate
+    on held-out pairs against the gravity-only guess, then run the network on
+    a rotating drum with DEM fallback.  Returns a dict of the results."""
+    import time
+    from . import batch, scenes
+    rng = np.random.default_rng(seed)
+    ns = [int(n) for n in np.exp(rng.uniform(math.log(800), math.log(3000), n_scenes))]
+    mus = [(float(rng.uniform(0.2, 0.8)), float(rng.uniform(0, 0.2)),
+            float(rng.uniform(0, 0.2))) for _ in ns]
+    b = batch.combine([batch.hopper_scene(n, 700 + k, mus[k]) for k, n in enumerate(ns)])
+    dt = b["params"]["dt"]
+    t0 = time.perf_counter()
+    pairs, R = sample_pairs(b, n_train + n_eval, every=100, settle=3000)
+    t_data = time.perf_counter() - t0
+    model = MPNN(seed=seed)
+    t0 = time.perf_counter()
+    hist = train(model, pairs[:n_train], R, dt, iters=iters, lr=lr, lr_end=lr / 10,
+                 log_every=max(1, iters // 12))
+    t_train = time.perf_counter() - t0
+    gv = np.asarray(b["params"]["g"])
+    e_net, e_base = evaluate(model, pairs[n_train:], R, dt, gv)
+    t_net_mse, t_base_mse = evaluate(model, pairs[:n_train], R, dt, gv)
+    # the network on a drum (another geometry), with DEM fallback
+    d = scenes.drum_scene(n=drum_n, seed=5, n_theta=64, n_rings=8, nn_dist=2.15e-3, speed=0.02)
+    sc = _dem.Scene.from_dict(d, precision=1)
+    sc.step(1500)
+    st = sc.state()
+    # DEM time for one stride of the drum, graph replay (device)
+    sc.synchronize()
+    t0 = time.perf_counter()
+    sc.step(100)
+    sc.synchronize()
+    dem_stride_ms = (time.perf_counter() - t0) * 1e3 / 10
+    sc.close()
+    _mesh_kw.clear()
+    _mesh_kw.update(verts=d["verts"], tris=d["tris"], tri_radius=d["tri_radius"])
+    roll = rollout(model, st, d["R"], d["params"], strides)
+    # network time for one stride of the drum: graph + forward
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(5):
+        predict(model, st, d["R"])
+    torch.cuda.synchronize()
+    net_stride_ms = (time.perf_counter() - t0) * 1e3 / 5
+    return {"train_particles": int(len(R)), "train_pairs": n_train, "eval_pairs": n_eval,
+            "iters": iters, "loss_history": hist, "eval_mse_net": e_net,
+            "eval_mse_gravity_only": e_base, "train_mse_net": t_net_mse,
+            "train_mse_gravity_only": t_base_mse, "data_s": t_data, "train_s": t_train,
+            "drum_particles": drum_n, "rollout": roll,
+            "net_ms_per_stride": net_stride_ms, "dem_ms_per_stride": dem_stride_ms}
+
+
+def main():
+    import json
+    import argparse
+    ap = argparse.ArgumentParser(description="train and run the surrogate")
+    ap.add_argument("--iters", type=int, default=3000)
+    ap.add_argument("--drum-n", type=int, default=20_000)
+    ap.add_argument("--strides", type=int, default=10)
+    a = ap.parse_args()
+    print(json.dumps(experiment(iters=a.iters, drum_n=a.drum_n, strides=a.strides)))
+
+
+if __name__ == "__main__":
+    main()

@@ -112,3 +112,26 @@ def test_training_reduces_the_loss(sg):
         model.adam(2e-3)
     last = model.loss_and_grad(g, buf)
     assert last < 0.2 * first, (first, last)
+
+
+def test_rollout_falls_back_to_the_dem_exactly(sg):
+    from paper_2507_12610_gb300 import dem, scenes
+    d = scenes.drum_scene(n=3000, seed=5, n_theta=32, n_rings=4, nn_dist=2.15e-3,
+                          radius=0.04, speed=0.02)
+    sc = dem.Scene.from_dict(d, precision=1)
+    sc.step(300)
+    st = sc.state()
+    sc.close()
+    sg._mesh_kw.clear()
+    sg._mesh_kw.update(verts=d["verts"], tris=d["tris"], tri_radius=d["tri_radius"])
+    model = sg.MPNN(seed=1)
+    # a threshold no stride can meet: every stride is the DEM's, so the hybrid
+    # run is the DEM run
+    r = sg.rollout(model, st, d["R"], d["params"], 3, overlap_growth=-1.0)
+    assert r["fallbacks"] == 3
+    assert all(e == 0.0 for _, e, _ in r["pos_error_rms_over_rmax"])
+    # thresholds no stride can miss: the network alone, close to the DEM after
+    # one stride of 10 steps
+    r = sg.rollout(model, st, d["R"], d["params"], 1, overlap_growth=1e9, energy_limit=1e9)
+    assert r["fallbacks"] == 0
+    assert 0.0 < r["pos_error_rms_over_rmax"][0][1] < 0.05
