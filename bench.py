@@ -168,13 +168,17 @@ def algorithmic_bytes(n: int, st: dict, mixed: bool) -> int:
 
 
 def kernel_sources_sha1() -> str:
+    """Hash of the sources the step kernels are compiled from (their .cu files
+    and the headers they include); a committed profile counts only while it
+    matches."""
     import hashlib
     d = os.path.join(ROOT, "paper_2507_12610_gb300", "csrc")
+    files = ["dem_step.cu", "dem_step_fp64.cu", "dem_step_warp.cuh", "dem_step_common.cuh",
+             "dem_law.cuh", "dem_geom.cuh", "dem_math.cuh", "dem_internal.cuh"]
     h = hashlib.sha1()
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh")):
-            with open(os.path.join(d, f), "rb") as fh:
-                h.update(f.encode() + b"\0" + fh.read())
+    for f in files:
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(f.encode() + b"\0" + fh.read())
     return h.hexdigest()
 
 
