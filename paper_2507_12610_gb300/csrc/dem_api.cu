@@ -39,6 +39,13 @@ struct Alloc {
   }
 };
 
+// DEM_FP64_TWO_SIDED=1 in the environment evaluates every pair from both of
+// its particles in one kernel (the scheme of DEM_MIXED) instead of once.
+bool fp64_two_sided() {
+  const char* env = std::getenv("DEM_FP64_TWO_SIDED");
+  return env && env[0] == '1';
+}
+
 bool finite_all(const double* a, int64_t n) {
   for (int64_t i = 0; i < n; ++i)
     if (!std::isfinite(a[i])) return false;
@@ -822,6 +829,7 @@ int dem_scene_create(const dem_params* params, const dem_particles* parts, const
     lb.offs = M.get<uint32_t>(n + 1);
     lb.nbr = M.get<uint32_t>((size_t)p.cap * n);
     lb.hpp = M.get<unsigned char>((size_t)p.cap * n * s->hist_bytes);
+    if (!p.mixed) lb.mir = M.get<uint32_t>((size_t)p.cap * n);
     if (has_mesh) {
       lb.tric = M.get<uint32_t>((size_t)p.capm * n);
       lb.hpm = M.get<unsigned char>((size_t)p.capm * n * s->hist_bytes);
@@ -838,6 +846,10 @@ int dem_scene_create(const dem_params* params, const dem_particles* parts, const
   s->bb.tmp_cnt = M.get<uint32_t>(n);
   s->bb.tmp_offs = M.get<uint32_t>(n + 1);
   if (p.record_forces) s->forces = M.get<double>(6 * (size_t)n);
+  if (!p.mixed && !fp64_two_sided()) {  // DEM_FP64: one evaluation per pair
+    p.pair_res = M.get<unsigned char>((size_t)p.cap * n * pair_result_bytes());
+    p.pair_stamp = M.get<uint32_t>((size_t)p.cap * n);
+  }
   if (has_mesh) {
     s->bb.tcell_count = M.get<uint32_t>(ncells);
     s->bb.tcell_start = M.get<uint32_t>(ncells + 1);
@@ -1118,8 +1130,9 @@ int dem_get_stats(dem_scene* s, dem_stats* out) {
   out->status = (int32_t)c.status;
   out->active = c.n_active;
   out->capacity = s->n;
-  const int32_t rebuild_launches = 15 + (s->nt > 0 ? 9 : 0);
-  const int32_t base = (s->static_mesh ? 0 : 1) + 2 + (s->p.sp_attempts > 0 ? 1 : 0);
+  const int32_t rebuild_launches = 15 + (s->nt > 0 ? 9 : 0) + (s->p.pair_res ? 1 : 0);
+  const int32_t base = (s->static_mesh ? 0 : 1) + 2 + (s->p.sp_attempts > 0 ? 1 : 0) +
+                       (s->p.pair_res ? 1 : 0);
   if (s->conditional_graphs) {
     out->launches_per_step = base + 1;
     out->launches_per_rebuild = rebuild_launches;

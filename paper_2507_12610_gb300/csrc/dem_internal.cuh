@@ -85,6 +85,9 @@ struct Params {
   // friction per material (n_mat = 0: the coefficients above); the material
   // index of a particle is in its W record (mixed: lo.w as int bits; FP64: w)
   int32_t step_warps;       // warps per block of the step kernel (4 or 8)
+  // DEM_FP64 one-evaluation-per-pair scheme (NULL: both sides evaluate)
+  void* pair_res;           // [list capacity] per-entry pair results
+  uint32_t* pair_stamp;     // [list capacity] step stamp of each result
   int32_t n_mat;
   const float4* mat_f;      // [n_mat] mu_s, mu_r, mu_t, 0
   const D4* mat_d;          // [n_mat] mu_s, mu_r, mu_t, 0
@@ -142,6 +145,8 @@ struct ListBuf {
   void* hpp;        // [offs[n]] pair history (HistD or HistM), one record per entry
   uint32_t* tric;   // [capm][n] candidate triangles, ascending
   void* hpm;        // [capm][n] triangle history
+  uint32_t* mir;    // [offs[n]] for an entry whose partner has the lower caller index,
+                    // the partner's entry for the same pair (DEM_FP64 only)
 };
 
 // Mesh at the current pose.
@@ -202,6 +207,8 @@ struct Lists {
 __device__ __forceinline__ void* buf_of(void* const (&a)[2], uint32_t b) {
   return b ? a[1] : a[0];
 }
+size_t pair_result_bytes();
+
 __device__ __forceinline__ ListBuf list_of(const Lists& L, uint32_t b) {
   ListBuf r;
   r.gid = b ? L.b[1].gid : L.b[0].gid;
@@ -212,6 +219,7 @@ __device__ __forceinline__ ListBuf list_of(const Lists& L, uint32_t b) {
   r.hpp = b ? L.b[1].hpp : L.b[0].hpp;
   r.tric = b ? L.b[1].tric : L.b[0].tric;
   r.hpm = b ? L.b[1].hpm : L.b[0].hpm;
+  r.mir = b ? L.b[1].mir : L.b[0].mir;
   return r;
 }
 #endif

@@ -407,6 +407,32 @@ inline unsigned blocks_for(int64_t n, int threads) {
 
 }  // namespace
 
+// For every entry whose partner u has the lower caller index, the index of
+// u's entry for the same pair: u's list is sorted by partner caller index, so
+// a binary search over its upper entries finds this particle.
+__global__ void __launch_bounds__(128)
+k_mirror(Ctl* ctl, Params p, Lists L) {
+  if (!rebuilding(ctl)) return;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= p.n) return;
+  const ListBuf ln = list_of(L, (ctl->lphase & 1u) ^ 1u);
+  const uint32_t meta = ln.meta[t];
+  const uint32_t nlow = (meta >> 8) & 0xffu;
+  const uint32_t off = ln.offs[t];
+  const uint32_t gt = ln.gid[t];
+  for (uint32_t k = 0; k < nlow; ++k) {
+    const uint32_t u = ln.nbr[off + k];
+    const uint32_t mu = ln.meta[u];
+    uint32_t lo = ln.offs[u] + ((mu >> 8) & 0xffu), hi = ln.offs[u] + (mu & 0xffu);
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (ln.gid[ln.nbr[mid]] < gt) lo = mid + 1;
+      else hi = mid;
+    }
+    ln.mir[off + k] = lo;
+  }
+}
+
 void launch_rebuild(cudaStream_t st, Ctl* ctl, const Params& p, StateBufs sb, Lists L,
                     BinBuf bb, MeshDev mesh) {
   const unsigned nb = blocks_for(p.n, kThreads);
@@ -441,6 +467,7 @@ void launch_rebuild(cudaStream_t st, Ctl* ctl, const Params& p, StateBufs sb, Li
     k_list_compact<HistM><<<nb128p, 128, 0, st>>>(ctl, p, bb, L);
   else
     k_list_compact<HistD><<<nb128p, 128, 0, st>>>(ctl, p, bb, L);
+  if (p.pair_res) k_mirror<<<nb128, 128, 0, st>>>(ctl, p, L);
   k_rebuild_end<<<1, 1, 0, st>>>(ctl, p);
 }
 

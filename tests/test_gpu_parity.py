@@ -254,3 +254,22 @@ def test_momentum_conserved_at_scale(dem):
         tol = 1e-12 if prec == 0 else 2e-6
         assert np.abs(p1 - p0).max() <= tol * scale, prec
         assert sc.stats()["pair_contacts"] > 10000
+
+
+def test_fp64_one_evaluation_per_pair_is_bitwise_the_two_sided_scheme(dem, monkeypatch):
+    # DEM_FP64 evaluates each pair once and hands the result to the partner;
+    # the environment switch selects the scheme that evaluates it from both
+    # sides.  Same values, summed in the same order: the same bits.
+    s = SCENES["drum_small"]()
+    out = []
+    for two in ("0", "1"):
+        monkeypatch.setenv("DEM_FP64_TWO_SIDED", two)
+        sc = dem.Scene.from_dict(s, precision=0, record_forces=True)
+        sc.step(150)
+        st = sc.state()
+        out.append((st, sc.forces(), sc.contacts(), sc.stats()))
+    for key in ("x", "v", "w", "q"):
+        assert np.array_equal(out[0][0][key], out[1][0][key]), key
+    assert np.array_equal(out[0][1][0], out[1][1][0]) and np.array_equal(out[0][1][1], out[1][1][1])
+    assert np.array_equal(out[0][2][0], out[1][2][0]) and np.array_equal(out[0][2][1], out[1][2][1])
+    assert out[0][3]["pair_contacts"] == out[1][3]["pair_contacts"] > 0
