@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--batch-steps", type=int, default=500)
     ap.add_argument("--batch-settle", type=int, default=3000)
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--skin", type=float, default=0.0, help="Verlet skin (m); 0: 0.25 R_max")
     return ap.parse_args()
 
 
@@ -239,7 +240,7 @@ def bench_ours(a):
     s_set = dict(s, x=settled["x"], v=settled["v"], w=settled["w"], q=settled["q"])
 
     with torch.cuda.stream(strm):
-        sc = dem.Scene.from_dict(s_set, precision=prec)
+        sc = dem.Scene.from_dict(s_set, precision=prec, skin=a.skin)
     sc.step(a.warmup)
     assert sc.synchronize() == 0, "warm-up failed"
     st0 = sc.stats()

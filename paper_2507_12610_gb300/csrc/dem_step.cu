@@ -37,7 +37,11 @@ __global__ void k_mesh_pose(const Ctl* ctl, Params p, MeshDev mesh) {
   const int nvk = tv.w >= 0 ? 4 : (tv.z >= 0 ? 3 : (tv.y >= 0 ? 2 : 1));
   const double rad = mesh.rad[k];
   const double wn = p.omega_norm;
-  const double c = ctl->rot_c, s = ctl->rot_s;
+  // the pose of this step; every thread evaluates the same expression (the
+  // same bits as k_set_pose), which keeps the one-thread step kernels free of
+  // FP64 transcendentals
+  const double th = p.omega_norm * ((double)ctl->step * p.dt);
+  const double c = wn > 0.0 ? cos(th) : 1.0, s = wn > 0.0 ? sin(th) : 0.0;
   const V3<double> ax =
       wn > 0.0 ? (1.0 / wn) * mk(p.mesh_omega[0], p.mesh_omega[1], p.mesh_omega[2])
                : mk(0.0, 0.0, 0.0);
@@ -104,11 +108,10 @@ __global__ void k_advance(Ctl* ctl, Params p) {
   // axis moves by the chord 2 r |sin(dtheta / 2)|
   bool mesh_moved = false;
   if (p.omega_norm > 0.0) {
+    // the chord 2 r |sin(dtheta / 2)| is at most r |dtheta|: a bound that
+    // asks for the rebuild no later than the chord itself would
     const double th = p.omega_norm * ((double)ctl->step * p.dt);
-    ctl->rot_c = cos(th);  // pose of the next step
-    ctl->rot_s = sin(th);
-    const double chord = 2.0 * p.mesh_rmax * fabs(sin(0.5 * (th - ctl->mesh_angle_ref)));
-    mesh_moved = chord >= (double)p.half_skin_trigger;
+    mesh_moved = p.mesh_rmax * fabs(th - ctl->mesh_angle_ref) >= (double)p.half_skin_trigger;
   }
   ctl->rebuild = (ctl->disp_flag || ctl->force_rebuild || mesh_moved) ? 1u : 0u;
   ctl->disp_flag = 0u;
@@ -507,7 +510,8 @@ struct MixedPolicy {
 
 void launch_mesh_pose(cudaStream_t st, const Ctl* ctl, const Params& p, MeshDev mesh) {
   if (mesh.nt <= 0) return;
-  k_mesh_pose<<<(unsigned)((mesh.nt + 127) / 128), 128, 0, st>>>(ctl, p, mesh);
+  // small blocks spread the elements over many SMs (the kernel is FP64 latency)
+  k_mesh_pose<<<(unsigned)((mesh.nt + 31) / 32), 32, 0, st>>>(ctl, p, mesh);
 }
 
 void launch_step(cudaStream_t st, Ctl* ctl, const Params& p, StateBufs sb, Lists L,
