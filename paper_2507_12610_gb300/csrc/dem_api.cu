@@ -502,6 +502,17 @@ int install_contacts(dem_scene* s, const std::vector<ContactRow>& rows, uint32_t
 
 // Upload a state given in caller order (slot = caller index) into buffer 0,
 // reset the control block to (step, lphase 0), and request a rebuild.
+// History records of both list buffers to "no contact" (stamp kStampNone in
+// every byte pattern 0xff); after this, a record counts only once written.
+int clear_histories(dem_scene* s) {
+  for (int b = 0; b < 2; ++b) {
+    const ListBuf& lb = s->L.b[b];
+    DEM_TRY(cudaMemset(lb.hpp, 0xff, (size_t)s->p.cap * s->n * s->hist_bytes));
+    if (lb.hpm) DEM_TRY(cudaMemset(lb.hpm, 0xff, (size_t)s->p.capm * s->n * s->hist_bytes));
+  }
+  return DEM_OK;
+}
+
 int upload_state(dem_scene* s, const double* x, const double* v, const double* w,
                  const double* q, const double* R, const int32_t* mat, int64_t step,
                  int64_t n_active, double spawn_carry, uint64_t spawn_draws) {
@@ -556,6 +567,10 @@ int upload_state(dem_scene* s, const double* x, const double* v, const double* w
     DEM_TRY(cudaMemcpy(s->L.b[b].gid, ident.data(), n * 4, cudaMemcpyHostToDevice));
     DEM_TRY(cudaMemset(s->L.b[b].meta, 0, n * 4));
     DEM_TRY(cudaMemset(s->L.b[b].offs, 0, (n + 1) * 4));
+  }
+  {
+    const int rc = clear_histories(s);
+    if (rc != DEM_OK) return rc;
   }
   Ctl c{};
   c.step = step;
@@ -1269,7 +1284,9 @@ int dem_load(dem_scene* s, const void* buf, size_t len) {
     DEM_TRY(cudaMemset(s->L.b[b].meta, 0, n * 4));
     DEM_TRY(cudaMemset(s->L.b[b].offs, 0, (n + 1) * 4));
   }
-  int rc = install_contacts(s, rows, 0, (uint32_t)step);
+  int rc = clear_histories(s);
+  if (rc != DEM_OK) return rc;
+  rc = install_contacts(s, rows, 0, (uint32_t)step);
   if (rc != DEM_OK) return rc;
   Ctl c{};
   c.step = step;

@@ -197,30 +197,58 @@ __global__ void k_tri_cells_check(Ctl* ctl, Params p, BinBuf bb) {
   }
 }
 
-__global__ void __launch_bounds__(kThreads)
+// Order each cell's element list by element index.  One warp per cell: every
+// lane ranks its elements against the whole list (indices in a cell are
+// distinct, so ranks are a permutation) and writes them to their ranks; a few
+// cells (around fan centres) hold a hundred elements or more, which a serial
+// insertion sort per cell would make the slowest step of the rebuild.
+constexpr int kSortWarps = 8;
+constexpr int kSortMax = 512;  // longer lists (not met in practice) sort serially
+
+__global__ void __launch_bounds__(32 * kSortWarps)
 k_tri_cell_sort(const Ctl* ctl, Params p, BinBuf bb) {
+  __shared__ uint32_t buf_s[kSortWarps][kSortMax];
   if (!rebuilding(ctl)) return;
-  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < p.ncells;
-       c += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t a = bb.tcell_start[c], b = bb.tcell_start[c + 1];
-    for (uint32_t i = a + 1; i < b; ++i) {
-      const uint32_t v = bb.tcell_tri[i];
-      uint32_t j = i;
-      while (j > a && bb.tcell_tri[j - 1] > v) {
-        bb.tcell_tri[j] = bb.tcell_tri[j - 1];
-        --j;
-      }
-      bb.tcell_tri[j] = v;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  uint32_t* buf = buf_s[wib];
+  const int64_t nw = (int64_t)gridDim.x * kSortWarps;
+  for (int64_t c = (int64_t)blockIdx.x * kSortWarps + wib; c < p.ncells; c += nw) {
+    const uint32_t a = bb.tcell_start[c], b = min(bb.tcell_start[c + 1], bb.tcap);
+    if (b <= a + 1) continue;
+    const uint32_t m = b - a;
+    if (m > (uint32_t)kSortMax) {
+      if (lane == 0)
+        for (uint32_t i = a + 1; i < b; ++i) {
+          const uint32_t v = bb.tcell_tri[i];
+          uint32_t j = i;
+          while (j > a && bb.tcell_tri[j - 1] > v) {
+            bb.tcell_tri[j] = bb.tcell_tri[j - 1];
+            --j;
+          }
+          bb.tcell_tri[j] = v;
+        }
+      __syncwarp();
+      continue;
     }
+    for (uint32_t i = lane; i < m; i += 32) buf[i] = bb.tcell_tri[a + i];
+    __syncwarp();
+    for (uint32_t i = lane; i < m; i += 32) {
+      const uint32_t v = buf[i];
+      uint32_t r = 0;
+      for (uint32_t j = 0; j < m; ++j) r += buf[j] < v ? 1u : 0u;
+      bb.tcell_tri[a + r] = v;
+    }
+    __syncwarp();
   }
 }
 
 // ---- Verlet list build + history remap -----------------------------------------
 
-template <typename Hist>
-__device__ __forceinline__ void mark_empty(Hist* h) {
-  h->stamp = kStampNone;
-}
+// History records are never cleared: a record counts only if its stamp is
+// the current step, and a record left in a list buffer from an earlier list
+// generation carries a stamp of at most the step that generation ended in,
+// which is before the current one.  The buffers start filled with kStampNone
+// (at creation and at a load).
 
 // For one new slot t: collect the partners within R_t + R_u + skin (float test
 // with a conservative margin) from the 27 surrounding cells, sorted by caller
@@ -324,13 +352,9 @@ k_list_build(Ctl* ctl, Params p, BinBuf bb, Lists L, MeshDev mesh) {
       }
       ln.tric[(size_t)ntc * n + t] = k;
       while (ko2 < nt_o && lo.tric[(size_t)ko2 * n + s] < k) ++ko2;
-      Hist* dst = &hpm_n[(size_t)ntc * n + t];
       if (ko2 < nt_o && lo.tric[(size_t)ko2 * n + s] == k) {
         const Hist h = hpm_o[(size_t)ko2 * n + s];
-        if (h.stamp == stamp_now) *dst = h;
-        else mark_empty(dst);
-      } else {
-        mark_empty(dst);
+        if (h.stamp == stamp_now) hpm_n[(size_t)ntc * n + t] = h;
       }
       ++ntc;
     }
@@ -365,9 +389,12 @@ k_list_compact(Ctl* ctl, Params p, BinBuf bb, Lists L) {
   const Hist* hpp_o = static_cast<const Hist*>(lo.hpp);
   Hist* hpp_n = static_cast<Hist*>(ln.hpp);
   const uint32_t stamp_now = (uint32_t)ctl->step;
+  // with one evaluation per pair only the upper entries carry history
+  const int k0 = p.pair_res ? (int)((ln.meta[t] >> 8) & 0xffu) : 0;
+  for (int k = 0; k < k0; ++k) ln.nbr[off + k] = bb.tmp_nbr[(size_t)k * n + t];
   int ko = 0;
   uint32_t go = ko < nn_o ? lo.gid[lo.nbr[off_o + ko]] : 0xffffffffu;
-  for (int k = 0; k < cnt; ++k) {
+  for (int k = k0; k < cnt; ++k) {
     const uint32_t u = bb.tmp_nbr[(size_t)k * n + t];
     const uint32_t g = ln.gid[u];
     ln.nbr[off + k] = u;
@@ -375,13 +402,9 @@ k_list_compact(Ctl* ctl, Params p, BinBuf bb, Lists L) {
       ++ko;
       go = ko < nn_o ? lo.gid[lo.nbr[off_o + ko]] : 0xffffffffu;
     }
-    Hist* dst = &hpp_n[off + k];
     if (ko < nn_o && go == g) {
       const Hist h = hpp_o[off_o + ko];
-      if (h.stamp == stamp_now) *dst = h;
-      else mark_empty(dst);
-    } else {
-      mark_empty(dst);
+      if (h.stamp == stamp_now) hpp_n[off + k] = h;
     }
   }
 }
@@ -454,7 +477,7 @@ void launch_rebuild(cudaStream_t st, Ctl* ctl, const Params& p, StateBufs sb, Li
     k_tri_cells_check<<<1, 1, 0, st>>>(ctl, p, bb);
     k_clear<<<gcells, kThreads, 0, st>>>(ctl, bb.tcell_count, p.ncells);
     k_tri_cells<<<(unsigned)mesh.nt, 128, 0, st>>>(ctl, p, mesh, bb, 1);
-    k_tri_cell_sort<<<gcells, kThreads, 0, st>>>(ctl, p, bb);
+    k_tri_cell_sort<<<152 * 8, 32 * kSortWarps, 0, st>>>(ctl, p, bb);
   }
   const unsigned nb128 = blocks_for(p.n, 128);
   const unsigned nb128p = blocks_for((int64_t)p.n + 1, 128);
