@@ -901,6 +901,7 @@ int dem_scene_create(const dem_params* params, const dem_particles* parts, const
     s->mesh.curf = M.get<float4>(4 * (size_t)s->nt);
     s->mesh.curl = M.get<float4>(4 * (size_t)s->nt);
     s->mesh.plane = M.get<float4>(2 * (size_t)s->nt);
+    s->mesh.nref = M.get<D4>(s->nt);
   }
   if (parts->n_materials > 0) {
     p.n_mat = parts->n_materials;
@@ -928,7 +929,21 @@ int dem_scene_create(const dem_params* params, const dem_particles* parts, const
     std::vector<D4> ref(s->nv);
     for (int k = 0; k < s->nv; ++k)
       ref[k] = make_D4(mesh->vert[3 * k], mesh->vert[3 * k + 1], mesh->vert[3 * k + 2], 0);
+    // face normals at the reference pose: (V1 - V0) x (V2 - V0), or V3 for the
+    // far corner of a rectangle; the pose kernel rotates them with the vertices
+    std::vector<D4> nref(s->nt, make_D4(0, 0, 0, 0));
+    for (int k = 0; k < s->nt; ++k) {
+      const int4 e = et.el[k];
+      if (e.z < 0) continue;
+      const D4 a = ref[e.x], b = ref[e.y], c = ref[e.w >= 0 ? e.w : e.z];
+      const double ux = b.x - a.x, uy = b.y - a.y, uz = b.z - a.z;
+      const double vx = c.x - a.x, vy = c.y - a.y, vz = c.z - a.z;
+      const double nx = uy * vz - uz * vy, ny = uz * vx - ux * vz, nz = ux * vy - uy * vx;
+      const double len = std::sqrt(nx * nx + ny * ny + nz * nz);
+      if (len > 0.0) nref[k] = make_D4(nx / len, ny / len, nz / len, 0);
+    }
     if (cudaMemcpy(s->mesh.ref, ref.data(), s->nv * sizeof(D4), cudaMemcpyHostToDevice) ||
+        cudaMemcpy(s->mesh.nref, nref.data(), s->nt * sizeof(D4), cudaMemcpyHostToDevice) ||
         cudaMemcpy(s->mesh.tri, et.el.data(), s->nt * sizeof(int4), cudaMemcpyHostToDevice) ||
         cudaMemcpy(s->mesh.rad, et.rad.data(), s->nt * sizeof(double), cudaMemcpyHostToDevice))
       return fail(DEM_ERR_CUDA);

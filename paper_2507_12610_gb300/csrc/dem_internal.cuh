@@ -162,6 +162,8 @@ struct MeshDev {
                      // vertex to ~1e-15); .w of slots 0, 1 = radius (hi, lo)
   float4* plane;     // [nt][2] face plane n.X = c in shifted coordinates, unit n:
                      // (n hi, c hi), (n lo, c lo); zero for points and segments
+  D4* nref;          // [nt] unit normal of the face at the reference pose (zero for
+                     // points, segments and degenerate faces)
   int32_t nv, nt;
 };
 

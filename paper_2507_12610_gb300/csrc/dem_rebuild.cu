@@ -257,59 +257,50 @@ k_tri_cell_sort(const Ctl* ctl, Params p, BinBuf bb) {
 // contact's history over from the particle's previous list.  The pair list is
 // packed into CSR form by k_list_compact once the counts are scanned.
 template <typename Hist>
-__global__ void __launch_bounds__(128)
-k_list_build(Ctl* ctl, Params p, BinBuf bb, Lists L, MeshDev mesh) {
-  if (!rebuilding(ctl)) return;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= p.n) return;
+__device__ __forceinline__ void list_one(Ctl* ctl, const Params& p, const BinBuf& bb,
+                                         const Lists& L, const MeshDev& mesh, int t,
+                                         const float4 X, int& cnt, int& ntc) {
   const ListBuf lo = list_of(L, ctl->lphase & 1u);
   const ListBuf ln = list_of(L, (ctl->lphase & 1u) ^ 1u);
   const int n = p.n;
-  const float4 X = ln.posf[t];
-  if (X.w == 0.f) {  // inactive: no list, no mesh candidates
-    bb.tmp_cnt[t] = 0u;
-    ln.meta[t] = 0u;
-    return;
-  }
   const uint32_t gt = ln.gid[t];
   const int3 c = cell_coords(p, X.x, X.y, X.z);
 
   uint32_t cand_g[64];
   uint32_t cand_s[64];
   const int cap = min(p.cap, 64);
-  int cnt = 0;
+  cnt = 0;
   bool overflow = false;
+  // the three cells of a row along x are consecutive in the grid, so their
+  // particles are one range of slots: 9 ranges for the 27 cells
+  const int x0 = max(c.x - 1, 0), x1 = min(c.x + 1, p.nc[0] - 1);
   for (int dz = -1; dz <= 1; ++dz) {
     const int cz = c.z + dz;
     if (cz < 0 || cz >= p.nc[2]) continue;
     for (int dy = -1; dy <= 1; ++dy) {
       const int cy = c.y + dy;
       if (cy < 0 || cy >= p.nc[1]) continue;
-      for (int dx = -1; dx <= 1; ++dx) {
-        const int cx = c.x + dx;
-        if (cx < 0 || cx >= p.nc[0]) continue;
-        const uint32_t cell = (uint32_t)((cz * p.nc[1] + cy) * p.nc[0] + cx);
-        const uint32_t a = bb.cell_start[cell], b = bb.cell_start[cell + 1];
-        for (uint32_t u = a; u < b; ++u) {
-          if (u == (uint32_t)t) continue;
-          const float4 Y = ln.posf[u];
-          const float ddx = X.x - Y.x, ddy = X.y - Y.y, ddz = X.z - Y.z;
-          const float cut = X.w + Y.w + p.skin + p.list_margin;
-          if (ddx * ddx + ddy * ddy + ddz * ddz < cut * cut) {
-            if (cnt < cap) {
-              const uint32_t g = ln.gid[u];
-              int j = cnt;
-              while (j > 0 && cand_g[j - 1] > g) {
-                cand_g[j] = cand_g[j - 1];
-                cand_s[j] = cand_s[j - 1];
-                --j;
-              }
-              cand_g[j] = g;
-              cand_s[j] = u;
-              ++cnt;
-            } else {
-              overflow = true;
+      const uint32_t row = (uint32_t)((cz * p.nc[1] + cy) * p.nc[0]);
+      const uint32_t a = bb.cell_start[row + x0], b = bb.cell_start[row + x1 + 1];
+      for (uint32_t u = a; u < b; ++u) {
+        if (u == (uint32_t)t) continue;
+        const float4 Y = ln.posf[u];
+        const float ddx = X.x - Y.x, ddy = X.y - Y.y, ddz = X.z - Y.z;
+        const float cut = X.w + Y.w + p.skin + p.list_margin;
+        if (ddx * ddx + ddy * ddy + ddz * ddz < cut * cut) {
+          if (cnt < cap) {
+            const uint32_t g = ln.gid[u];
+            int j = cnt;
+            while (j > 0 && cand_g[j - 1] > g) {
+              cand_g[j] = cand_g[j - 1];
+              cand_s[j] = cand_s[j - 1];
+              --j;
             }
+            cand_g[j] = g;
+            cand_s[j] = u;
+            ++cnt;
+          } else {
+            overflow = true;
           }
         }
       }
@@ -328,7 +319,7 @@ k_list_build(Ctl* ctl, Params p, BinBuf bb, Lists L, MeshDev mesh) {
   const uint32_t mo = lo.meta[s];
   const int nt_o = (int)((mo >> 16) & 0xffu);
   const uint32_t stamp_now = (uint32_t)ctl->step;  // records written in the previous step
-  int ntc = 0;
+  ntc = 0;
   if (mesh.nt > 0) {
     const uint32_t cell = cell_index(p, c);
     const uint32_t a = bb.tcell_start[cell], b = min(bb.tcell_start[cell + 1], bb.tcap);
@@ -361,9 +352,36 @@ k_list_build(Ctl* ctl, Params p, BinBuf bb, Lists L, MeshDev mesh) {
     if (tover) set_status(ctl, DEM_ERR_CAPACITY);
   }
   ln.meta[t] = (uint32_t)cnt | ((uint32_t)nlow << 8) | ((uint32_t)ntc << 16);
-  atomicAdd(&ctl->list_entries, (uint32_t)cnt);
-  atomicAdd(&ctl->mesh_candidates, (uint32_t)ntc);
-  atomicMax(&ctl->max_list_len, (uint32_t)cnt);
+}
+
+
+// One thread per new slot (list_one), then the list statistics.
+template <typename Hist>
+__global__ void __launch_bounds__(128)
+k_list_build(Ctl* ctl, Params p, BinBuf bb, Lists L, MeshDev mesh) {
+  if (!rebuilding(ctl)) return;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const ListBuf ln = list_of(L, (ctl->lphase & 1u) ^ 1u);
+  int cnt = 0, ntc = 0;
+  if (t < p.n) {
+    const float4 X = ln.posf[t];
+    if (X.w == 0.f) {  // inactive: no list, no mesh candidates
+      bb.tmp_cnt[t] = 0u;
+      ln.meta[t] = 0u;
+    } else {
+      list_one<Hist>(ctl, p, bb, L, mesh, t, X, cnt, ntc);
+    }
+  }
+  // the list statistics, one atomic per warp
+  const unsigned full = 0xffffffffu;
+  const uint32_t scnt = __reduce_add_sync(full, (uint32_t)cnt);
+  const uint32_t sntc = __reduce_add_sync(full, (uint32_t)ntc);
+  const uint32_t mcnt = __reduce_max_sync(full, (uint32_t)cnt);
+  if ((threadIdx.x & 31) == 0) {
+    if (scnt) atomicAdd(&ctl->list_entries, scnt);
+    if (sntc) atomicAdd(&ctl->mesh_candidates, sntc);
+    if (mcnt) atomicMax(&ctl->max_list_len, mcnt);
+  }
 }
 
 // Pack the new pair lists into CSR form (offsets from the scan of the counts)

@@ -28,7 +28,8 @@ namespace {
 
 // One thread per element: its vertices at the current pose (absolute in FP64;
 // shifted as hi + lo floats), and for triangles and rectangles the unit
-// normal and offset of its plane, split the same way.
+// normal (the reference normal, rotated) and offset of its plane, split the
+// same way.
 __global__ void k_mesh_pose(const Ctl* ctl, Params p, MeshDev mesh) {
   if (ctl->status) return;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -64,17 +65,15 @@ __global__ void k_mesh_pose(const Ctl* ctl, Params p, MeshDev mesh) {
     mesh.curl[4 * k + j] = make_float4((float)(X[j].x - hx), (float)(X[j].y - hy),
                                        (float)(X[j].z - hz), rw);
   }
+  // the face normal: the reference one, rotated like the vertices
   float4 ph = make_float4(0.f, 0.f, 0.f, 0.f), pl = ph;
   if (nvk >= 3) {
-    V3<double> nrm = cross(X[1] - X[0], (nvk == 4 ? X[3] : X[2]) - X[0]);
-    const double len = sqrt(dot(nrm, nrm));
-    if (len > 0.0) {
-      nrm = (1.0 / len) * nrm;
-      const double off = dot(nrm, X[0]);
-      ph = make_float4((float)nrm.x, (float)nrm.y, (float)nrm.z, (float)off);
-      pl = make_float4((float)(nrm.x - ph.x), (float)(nrm.y - ph.y), (float)(nrm.z - ph.z),
-                       (float)(off - ph.w));
-    }
+    V3<double> nrm = xyz(mesh.nref[k]);
+    if (wn > 0.0) nrm = c * nrm + s * cross(ax, nrm) + (dot(ax, nrm) * (1.0 - c)) * ax;
+    const double off = dot(nrm, X[0]);
+    ph = make_float4((float)nrm.x, (float)nrm.y, (float)nrm.z, (float)off);
+    pl = make_float4((float)(nrm.x - ph.x), (float)(nrm.y - ph.y), (float)(nrm.z - ph.z),
+                     (float)(off - ph.w));
   }
   mesh.plane[2 * k] = ph;
   mesh.plane[2 * k + 1] = pl;

@@ -1,6 +1,7 @@
 """The piling example (Sec. 5) at a small size: a spawned stream between two
 plates forms a heap with straight flanks; both precisions agree on its angle
 of repose and packing (the full-size statistics are a longer run)."""
+import numpy as np
 import pytest
 
 pytestmark = pytest.mark.gpu
@@ -18,13 +19,20 @@ def repose():
 
 
 def test_small_heap_in_both_precisions(repose):
-    out = {p: repose.run(n=3000, precision=p, max_time=3.0) for p in (0, 1)}
-    for r in out.values():
-        assert r["status"] == 0 and r["settled"] and r["active"] == 3000
-        # a small heap: flanks well below the large-heap angle, both alike
-        assert 20.0 < r["theta"] < 45.0
-        assert abs(r["theta_left"] - r["theta_right"]) < 6.0
-        assert 0.42 < r["packing_core"] < 0.62
-    # 3000 grains: one realisation each, a few per cent apart at most
-    assert abs(out[0]["theta"] - out[1]["theta"]) < 0.06 * out[0]["theta"]
-    assert abs(out[0]["packing_core"] - out[1]["packing_core"]) < 0.03
+    seeds = (7, 8, 9)
+    out = {p: [repose.run(n=3000, precision=p, seed=sd, max_time=3.0) for sd in seeds]
+           for p in (0, 1)}
+    for runs in out.values():
+        for r in runs:
+            assert r["status"] == 0 and r["settled"] and r["active"] == 3000
+            # a small heap: flanks well below the large-heap angle, both alike
+            assert 20.0 < r["theta"] < 45.0
+            assert abs(r["theta_left"] - r["theta_right"]) < 6.0
+            assert 0.42 < r["packing_core"] < 0.62
+    # A 3,000-grain heap is chaotic: a rounding-level change moves one
+    # realisation's angle by several per cent (29.1 and 27.2 degrees for the
+    # same seed), so the precisions are compared on the mean of three seeds.
+    mean = {p: np.mean([r["theta"] for r in runs]) for p, runs in out.items()}
+    pack = {p: np.mean([r["packing_core"] for r in runs]) for p, runs in out.items()}
+    assert abs(mean[0] - mean[1]) < 0.06 * mean[0]
+    assert abs(pack[0] - pack[1]) < 0.03
