@@ -141,8 +141,15 @@ struct dem_scene {
   MeshDev mesh{};
   double* forces = nullptr;
   Alloc mem;
-  cudaGraphExec_t exec1 = nullptr, execG = nullptr;
+  // step graphs (1 and kGraphSteps steps) for a start at an even / odd step:
+  // each captured step passes its kernels the pose buffers of its parity
+  cudaGraphExec_t exec1[2] = {nullptr, nullptr}, execG[2] = {nullptr, nullptr};
+  int64_t step_host = 0;  // the step the device is at once the queued work ends
   cudaStream_t aux = nullptr;  // captures the conditional rebuild bodies
+  // branch of a captured step that computes the next step's mesh pose beside
+  // the step kernel (fork and join events)
+  cudaStream_t pose_stream = nullptr;
+  cudaEvent_t pose_fork = nullptr, pose_join = nullptr;
   bool conditional_graphs = false;
   bool static_mesh = true;
 };
@@ -233,25 +240,50 @@ inline void split(double a, float& hi, float& lo) {
   lo = (float)(a - (double)hi);
 }
 
-// Enqueue one complete step on the stream.
-void enqueue_step(dem_scene* s) {
-  if (!s->static_mesh) launch_mesh_pose(s->stream, s->ctl, s->p, s->mesh);
-  launch_rebuild(s->stream, s->ctl, s->p, s->sb, s->L, s->bb, s->mesh);
-  launch_spawn(s->stream, s->ctl, s->p, s->sb, s->bb, s->mesh);
-  launch_step(s->stream, s->ctl, s->p, s->sb, s->L, s->mesh, s->forces);
+// The mesh pose of the step after `step`.  It depends on the step number
+// only, so in a capture it is a branch of its own beside the step's kernels
+// (joined before the step advances); the pose of the step itself is already
+// in its buffer (computed by the previous step, or at upload).
+cudaError_t fork_next_pose(dem_scene* s, int64_t step) {
+  if (s->static_mesh) return cudaSuccess;
+  cudaError_t e = cudaEventRecord(s->pose_fork, s->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s->pose_stream, s->pose_fork, 0);
+  if (e != cudaSuccess) return e;
+  launch_mesh_pose(s->pose_stream, s->ctl, s->p, mesh_at(s->mesh, step + 1), 1);
+  return cudaEventRecord(s->pose_join, s->pose_stream);
+}
+cudaError_t join_next_pose(dem_scene* s) {
+  if (s->static_mesh) return cudaSuccess;
+  return cudaStreamWaitEvent(s->stream, s->pose_join, 0);
+}
+
+// Enqueue one complete step on the stream (inside a capture); `step` is the
+// step number it will run at (only its parity matters).
+cudaError_t enqueue_step(dem_scene* s, int64_t step) {
+  cudaError_t e = fork_next_pose(s, step);
+  if (e != cudaSuccess) return e;
+  const MeshDev mesh = mesh_at(s->mesh, step);
+  launch_rebuild(s->stream, s->ctl, s->p, s->sb, s->L, s->bb, mesh);
+  launch_spawn(s->stream, s->ctl, s->p, s->sb, s->bb, mesh);
+  launch_step(s->stream, s->ctl, s->p, s->sb, s->L, mesh, s->forces);
+  e = join_next_pose(s);
+  if (e != cudaSuccess) return e;
   launch_advance(s->stream, s->ctl, s->p);
+  return cudaSuccess;
 }
 
 // One step inside a stream capture, with the rebuild kernels in the body of a
 // conditional (IF) graph node whose condition a one-thread kernel sets from
 // ctl->rebuild: steps without a rebuild then launch only the step kernels.
-cudaError_t enqueue_step_conditional(dem_scene* s) {
-  if (!s->static_mesh) launch_mesh_pose(s->stream, s->ctl, s->p, s->mesh);
+cudaError_t enqueue_step_conditional(dem_scene* s, int64_t step) {
+  cudaError_t e = fork_next_pose(s, step);
+  if (e != cudaSuccess) return e;
+  const MeshDev mesh = mesh_at(s->mesh, step);
   cudaStreamCaptureStatus cs;
   cudaGraph_t g = nullptr;
   const cudaGraphNode_t* deps = nullptr;
   size_t nd = 0;
-  cudaError_t e = cudaStreamGetCaptureInfo(s->stream, &cs, nullptr, &g, nullptr, nullptr, nullptr);
+  e = cudaStreamGetCaptureInfo(s->stream, &cs, nullptr, &g, nullptr, nullptr, nullptr);
   if (e != cudaSuccess) return e;
   cudaGraphConditionalHandle h;
   e = cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault);
@@ -271,20 +303,23 @@ cudaError_t enqueue_step_conditional(dem_scene* s) {
   e = cudaStreamBeginCaptureToGraph(s->aux, body, nullptr, nullptr, 0,
                                     cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return e;
-  launch_rebuild(s->aux, s->ctl, s->p, s->sb, s->L, s->bb, s->mesh);
+  launch_rebuild(s->aux, s->ctl, s->p, s->sb, s->L, s->bb, mesh);
   cudaGraph_t body_out = nullptr;
   e = cudaStreamEndCapture(s->aux, &body_out);
   if (e != cudaSuccess) return e;
   e = cudaStreamUpdateCaptureDependencies(s->stream, &node, nullptr, 1,
                                           cudaStreamSetCaptureDependencies);
   if (e != cudaSuccess) return e;
-  launch_spawn(s->stream, s->ctl, s->p, s->sb, s->bb, s->mesh);
-  launch_step(s->stream, s->ctl, s->p, s->sb, s->L, s->mesh, s->forces);
+  launch_spawn(s->stream, s->ctl, s->p, s->sb, s->bb, mesh);
+  launch_step(s->stream, s->ctl, s->p, s->sb, s->L, mesh, s->forces);
+  e = join_next_pose(s);
+  if (e != cudaSuccess) return e;
   launch_advance(s->stream, s->ctl, s->p);
   return cudaSuccess;
 }
 
-int build_graph(dem_scene* s, int nsteps, cudaGraphExec_t* out) {
+// A graph of nsteps steps that starts at a step of parity `odd`.
+int build_graph(dem_scene* s, int nsteps, int odd, cudaGraphExec_t* out) {
   // first choice: conditional rebuild bodies; fall back to the plain sequence
   // (rebuild kernels that return at once) if the driver refuses
   // DEM_GRAPH_CONDITIONAL=0 in the environment keeps every rebuild kernel a
@@ -297,8 +332,7 @@ int build_graph(dem_scene* s, int nsteps, cudaGraphExec_t* out) {
     DEM_TRY(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
     for (int i = 0; i < nsteps && e == cudaSuccess; ++i) {
-      if (cond) e = enqueue_step_conditional(s);
-      else enqueue_step(s);
+      e = cond ? enqueue_step_conditional(s, odd + i) : enqueue_step(s, odd + i);
     }
     const cudaError_t e2 = cudaStreamEndCapture(s->stream, &g);
     if (e == cudaSuccess && e2 == cudaSuccess) {
@@ -585,12 +619,17 @@ int upload_state(dem_scene* s, const double* x, const double* v, const double* w
 
 void destroy(dem_scene* s) {
   if (!s) return;
-  if (s->exec1) cudaGraphExecDestroy(s->exec1);
-  if (s->execG) cudaGraphExecDestroy(s->execG);
+  for (int b = 0; b < 2; ++b) {
+    if (s->exec1[b]) cudaGraphExecDestroy(s->exec1[b]);
+    if (s->execG[b]) cudaGraphExecDestroy(s->execG[b]);
+  }
   if (s->stream) cudaStreamSynchronize(s->stream);
   s->mem.release();
   if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
   if (s->aux) cudaStreamDestroy(s->aux);
+  if (s->pose_stream) cudaStreamDestroy(s->pose_stream);
+  if (s->pose_fork) cudaEventDestroy(s->pose_fork);
+  if (s->pose_join) cudaEventDestroy(s->pose_join);
   delete s;
 }
 
@@ -638,6 +677,10 @@ int dem_scene_create(const dem_params* params, const dem_particles* parts, const
     cudaGetLastError();
     s->aux = nullptr;
   }
+  if (cudaStreamCreateWithFlags(&s->pose_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&s->pose_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&s->pose_join, cudaEventDisableTiming) != cudaSuccess)
+    return fail(DEM_ERR_CUDA);
   s->user = *params;
   const int64_t n_init = parts->n;  // active at creation; rows n_init .. n-1 await spawning
   const bool spawning = params->spawn_attempts > 0;
@@ -902,6 +945,10 @@ int dem_scene_create(const dem_params* params, const dem_particles* parts, const
     s->mesh.curl = M.get<float4>(4 * (size_t)s->nt);
     s->mesh.plane = M.get<float4>(2 * (size_t)s->nt);
     s->mesh.nref = M.get<D4>(s->nt);
+    s->mesh.cur_odd = M.get<D4>(4 * (size_t)s->nt);
+    s->mesh.curf_odd = M.get<float4>(4 * (size_t)s->nt);
+    s->mesh.curl_odd = M.get<float4>(4 * (size_t)s->nt);
+    s->mesh.plane_odd = M.get<float4>(2 * (size_t)s->nt);
   }
   if (parts->n_materials > 0) {
     p.n_mat = parts->n_materials;
@@ -972,8 +1019,10 @@ int dem_scene_create(const dem_params* params, const dem_particles* parts, const
                       n_init, -1.0, 0);
   }
   if (rc != DEM_OK) return fail(rc);
-  // pose at step 0 (a static mesh keeps it)
-  launch_mesh_pose(s->stream, s->ctl, s->p, s->mesh);
+  // poses of steps 0 and 1 (a static mesh keeps them)
+  s->step_host = 0;
+  launch_mesh_pose(s->stream, s->ctl, s->p, mesh_at(s->mesh, 0), 0);
+  launch_mesh_pose(s->stream, s->ctl, s->p, mesh_at(s->mesh, 1), 1);
   if (cudaStreamSynchronize(s->stream) != cudaSuccess) return fail(DEM_ERR_CUDA);
   *out = s;
   return DEM_OK;
@@ -982,18 +1031,20 @@ int dem_scene_create(const dem_params* params, const dem_particles* parts, const
 int dem_step(dem_scene* s, int64_t nsteps) {
   if (!s || nsteps < 0) return DEM_ERR_INVALID;
   if (nsteps == 0) return DEM_OK;
-  if (!s->exec1) {
-    int rc = build_graph(s, 1, &s->exec1);
-    if (rc != DEM_OK) return rc;
-    rc = build_graph(s, kGraphSteps, &s->execG);
-    if (rc != DEM_OK) return rc;
-  }
+  // graphs are built on first use, per parity of the starting step
   int64_t left = nsteps;
-  while (left >= kGraphSteps) {
-    DEM_TRY(cudaGraphLaunch(s->execG, s->stream));
-    left -= kGraphSteps;
+  while (left > 0) {
+    const int odd = (int)(s->step_host & 1);
+    const int k = left >= kGraphSteps ? kGraphSteps : 1;
+    cudaGraphExec_t* ex = k == kGraphSteps ? s->execG : s->exec1;
+    if (!ex[odd]) {
+      const int rc = build_graph(s, k, odd, &ex[odd]);
+      if (rc != DEM_OK) return rc;
+    }
+    DEM_TRY(cudaGraphLaunch(ex[odd], s->stream));
+    left -= k;
+    s->step_host += k;
   }
-  while (left-- > 0) DEM_TRY(cudaGraphLaunch(s->exec1, s->stream));
   return DEM_OK;
 }
 
@@ -1008,15 +1059,19 @@ int dem_step_timed(dem_scene* s, int64_t nsteps, double* phase_ms) {
   int rc = DEM_OK;
   double acc[4] = {0, 0, 0, 0};
   for (int64_t k = 0; k < nsteps && rc == DEM_OK; ++k) {
+    // phase by phase on one stream; the pose timed is that of the next step
+    const MeshDev mesh = mesh_at(s->mesh, s->step_host);
     cudaEventRecord(ev[0], s->stream);
-    if (!s->static_mesh) launch_mesh_pose(s->stream, s->ctl, s->p, s->mesh);
+    if (!s->static_mesh)
+      launch_mesh_pose(s->stream, s->ctl, s->p, mesh_at(s->mesh, s->step_host + 1), 1);
     cudaEventRecord(ev[1], s->stream);
-    launch_rebuild(s->stream, s->ctl, s->p, s->sb, s->L, s->bb, s->mesh);
-    launch_spawn(s->stream, s->ctl, s->p, s->sb, s->bb, s->mesh);
+    launch_rebuild(s->stream, s->ctl, s->p, s->sb, s->L, s->bb, mesh);
+    launch_spawn(s->stream, s->ctl, s->p, s->sb, s->bb, mesh);
     cudaEventRecord(ev[2], s->stream);
-    launch_step(s->stream, s->ctl, s->p, s->sb, s->L, s->mesh, s->forces);
+    launch_step(s->stream, s->ctl, s->p, s->sb, s->L, mesh, s->forces);
     cudaEventRecord(ev[3], s->stream);
     launch_advance(s->stream, s->ctl, s->p);
+    ++s->step_host;
     cudaEventRecord(ev[4], s->stream);
     rc = cuda_status(cudaEventSynchronize(ev[4]));
     for (int i = 0; i < 4 && rc == DEM_OK; ++i) {
@@ -1311,7 +1366,9 @@ int dem_load(dem_scene* s, const void* buf, size_t len) {
   c.spawn_carry = carry;
   DEM_TRY(cudaMemcpy(s->ctl, &c, sizeof c, cudaMemcpyHostToDevice));
   launch_set_pose(s->stream, s->ctl, s->p);
-  launch_mesh_pose(s->stream, s->ctl, s->p, s->mesh);
+  s->step_host = step;
+  launch_mesh_pose(s->stream, s->ctl, s->p, mesh_at(s->mesh, step), 0);
+  launch_mesh_pose(s->stream, s->ctl, s->p, mesh_at(s->mesh, step + 1), 1);
   DEM_TRY(cudaStreamSynchronize(s->stream));
   return DEM_OK;
 }

@@ -149,9 +149,13 @@ struct ListBuf {
                     // the partner's entry for the same pair (DEM_FP64 only)
 };
 
-// Mesh at the current pose.
 // Mesh elements (Sec. 3.3): triangles first, then points, segments and
 // rectangles; four vertex slots per element, unused slots repeat vertex 0.
+// The pose arrays (cur, curf, curl, plane) hold the pose of an even step, the
+// *_odd arrays that of an odd step: the pose of step n + 1 is computed while
+// step n runs (it depends on the step number only).  The host passes each
+// kernel the view of its step (mesh_at), so kernels index no buffer by the
+// step at run time.
 struct MeshDev {
   D4* ref;           // [nv] reference vertices (x, y, z, 0)
   int4* tri;         // [nt] vertex indices, -1 for unused slots
@@ -164,6 +168,10 @@ struct MeshDev {
                      // (n hi, c hi), (n lo, c lo); zero for points and segments
   D4* nref;          // [nt] unit normal of the face at the reference pose (zero for
                      // points, segments and degenerate faces)
+  D4* cur_odd;       // the four pose arrays above, for odd steps
+  float4* curf_odd;
+  float4* curl_odd;
+  float4* plane_odd;
   int32_t nv, nt;
 };
 
@@ -211,6 +219,18 @@ __device__ __forceinline__ void* buf_of(void* const (&a)[2], uint32_t b) {
 }
 size_t pair_result_bytes();
 
+// The mesh with the pose arrays of step `step` (even or odd buffers).
+inline MeshDev mesh_at(const MeshDev& m, int64_t step) {
+  MeshDev r = m;
+  if (step & 1) {
+    r.cur = m.cur_odd;
+    r.curf = m.curf_odd;
+    r.curl = m.curl_odd;
+    r.plane = m.plane_odd;
+  }
+  return r;
+}
+
 __device__ __forceinline__ ListBuf list_of(const Lists& L, uint32_t b) {
   ListBuf r;
   r.gid = b ? L.b[1].gid : L.b[0].gid;
@@ -229,7 +249,9 @@ __device__ __forceinline__ ListBuf list_of(const Lists& L, uint32_t b) {
 // Kernel launch helpers implemented in the .cu files.
 void launch_spawn(cudaStream_t st, Ctl* ctl, const Params& p, StateBufs sb, BinBuf bb,
                   MeshDev mesh);
-void launch_mesh_pose(cudaStream_t st, const Ctl* ctl, const Params& p, MeshDev mesh);
+// The pose of step ctl->step + ahead (ahead 0 or 1) into the pose arrays of
+// `mesh` (the view of that step).
+void launch_mesh_pose(cudaStream_t st, const Ctl* ctl, const Params& p, MeshDev mesh, int ahead);
 void launch_rebuild(cudaStream_t st, Ctl* ctl, const Params& p, StateBufs sb, Lists L,
                     BinBuf bb, MeshDev mesh);
 void launch_step(cudaStream_t st, Ctl* ctl, const Params& p, StateBufs sb, Lists L,

@@ -257,19 +257,27 @@ k_tri_cell_sort(const Ctl* ctl, Params p, BinBuf bb) {
 // contact's history over from the particle's previous list.  The pair list is
 // packed into CSR form by k_list_compact once the counts are scanned.
 template <typename Hist>
-__device__ __forceinline__ void list_one(Ctl* ctl, const Params& p, const BinBuf& bb,
-                                         const Lists& L, const MeshDev& mesh, int t,
-                                         const float4 X, int& cnt, int& ntc) {
+__global__ void __launch_bounds__(128)
+k_list_build(Ctl* ctl, Params p, BinBuf bb, Lists L, MeshDev mesh) {
+  if (!rebuilding(ctl)) return;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= p.n) return;
   const ListBuf lo = list_of(L, ctl->lphase & 1u);
   const ListBuf ln = list_of(L, (ctl->lphase & 1u) ^ 1u);
   const int n = p.n;
+  const float4 X = ln.posf[t];
+  if (X.w == 0.f) {  // inactive: no list, no mesh candidates
+    bb.tmp_cnt[t] = 0u;
+    ln.meta[t] = 0u;
+    return;
+  }
   const uint32_t gt = ln.gid[t];
   const int3 c = cell_coords(p, X.x, X.y, X.z);
 
   uint32_t cand_g[64];
   uint32_t cand_s[64];
   const int cap = min(p.cap, 64);
-  cnt = 0;
+  int cnt = 0;
   bool overflow = false;
   // the three cells of a row along x are consecutive in the grid, so their
   // particles are one range of slots: 9 ranges for the 27 cells
@@ -319,7 +327,7 @@ __device__ __forceinline__ void list_one(Ctl* ctl, const Params& p, const BinBuf
   const uint32_t mo = lo.meta[s];
   const int nt_o = (int)((mo >> 16) & 0xffu);
   const uint32_t stamp_now = (uint32_t)ctl->step;  // records written in the previous step
-  ntc = 0;
+  int ntc = 0;
   if (mesh.nt > 0) {
     const uint32_t cell = cell_index(p, c);
     const uint32_t a = bb.tcell_start[cell], b = min(bb.tcell_start[cell + 1], bb.tcap);
@@ -352,36 +360,9 @@ __device__ __forceinline__ void list_one(Ctl* ctl, const Params& p, const BinBuf
     if (tover) set_status(ctl, DEM_ERR_CAPACITY);
   }
   ln.meta[t] = (uint32_t)cnt | ((uint32_t)nlow << 8) | ((uint32_t)ntc << 16);
-}
-
-
-// One thread per new slot (list_one), then the list statistics.
-template <typename Hist>
-__global__ void __launch_bounds__(128)
-k_list_build(Ctl* ctl, Params p, BinBuf bb, Lists L, MeshDev mesh) {
-  if (!rebuilding(ctl)) return;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  const ListBuf ln = list_of(L, (ctl->lphase & 1u) ^ 1u);
-  int cnt = 0, ntc = 0;
-  if (t < p.n) {
-    const float4 X = ln.posf[t];
-    if (X.w == 0.f) {  // inactive: no list, no mesh candidates
-      bb.tmp_cnt[t] = 0u;
-      ln.meta[t] = 0u;
-    } else {
-      list_one<Hist>(ctl, p, bb, L, mesh, t, X, cnt, ntc);
-    }
-  }
-  // the list statistics, one atomic per warp
-  const unsigned full = 0xffffffffu;
-  const uint32_t scnt = __reduce_add_sync(full, (uint32_t)cnt);
-  const uint32_t sntc = __reduce_add_sync(full, (uint32_t)ntc);
-  const uint32_t mcnt = __reduce_max_sync(full, (uint32_t)cnt);
-  if ((threadIdx.x & 31) == 0) {
-    if (scnt) atomicAdd(&ctl->list_entries, scnt);
-    if (sntc) atomicAdd(&ctl->mesh_candidates, sntc);
-    if (mcnt) atomicMax(&ctl->max_list_len, mcnt);
-  }
+  atomicAdd(&ctl->list_entries, (uint32_t)cnt);
+  atomicAdd(&ctl->mesh_candidates, (uint32_t)ntc);
+  atomicMax(&ctl->max_list_len, (uint32_t)cnt);
 }
 
 // Pack the new pair lists into CSR form (offsets from the scan of the counts)

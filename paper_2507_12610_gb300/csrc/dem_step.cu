@@ -26,14 +26,15 @@ namespace {
 
 // ---- mesh pose: reference vertices rotated by |Omega| t about the axis ------
 
-// One thread per element: its vertices at the current pose (absolute in FP64;
-// shifted as hi + lo floats), and for triangles and rectangles the unit
-// normal (the reference normal, rotated) and offset of its plane, split the
-// same way.
-__global__ void k_mesh_pose(const Ctl* ctl, Params p, MeshDev mesh) {
+// One thread per element: its vertices at the pose of step ctl->step + ahead
+// (absolute in FP64; shifted as hi + lo floats), and for triangles and
+// rectangles the unit normal (the reference normal, rotated) and offset of
+// its plane, split the same way.
+__global__ void k_mesh_pose(const Ctl* ctl, Params p, MeshDev mesh, int ahead) {
   if (ctl->status) return;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= mesh.nt) return;
+  const int64_t step = ctl->step + ahead;
   const int4 tv = mesh.tri[k];
   const int nvk = tv.w >= 0 ? 4 : (tv.z >= 0 ? 3 : (tv.y >= 0 ? 2 : 1));
   const double rad = mesh.rad[k];
@@ -41,7 +42,7 @@ __global__ void k_mesh_pose(const Ctl* ctl, Params p, MeshDev mesh) {
   // the pose of this step; every thread evaluates the same expression (the
   // same bits as k_set_pose), which keeps the one-thread step kernels free of
   // FP64 transcendentals
-  const double th = p.omega_norm * ((double)ctl->step * p.dt);
+  const double th = p.omega_norm * ((double)step * p.dt);
   const double c = wn > 0.0 ? cos(th) : 1.0, s = wn > 0.0 ? sin(th) : 0.0;
   const V3<double> ax =
       wn > 0.0 ? (1.0 / wn) * mk(p.mesh_omega[0], p.mesh_omega[1], p.mesh_omega[2])
@@ -507,10 +508,10 @@ struct MixedPolicy {
 
 }  // namespace
 
-void launch_mesh_pose(cudaStream_t st, const Ctl* ctl, const Params& p, MeshDev mesh) {
+void launch_mesh_pose(cudaStream_t st, const Ctl* ctl, const Params& p, MeshDev mesh, int ahead) {
   if (mesh.nt <= 0) return;
   // small blocks spread the elements over many SMs (the kernel is FP64 latency)
-  k_mesh_pose<<<(unsigned)((mesh.nt + 31) / 32), 32, 0, st>>>(ctl, p, mesh);
+  k_mesh_pose<<<(unsigned)((mesh.nt + 31) / 32), 32, 0, st>>>(ctl, p, mesh, ahead);
 }
 
 void launch_step(cudaStream_t st, Ctl* ctl, const Params& p, StateBufs sb, Lists L,

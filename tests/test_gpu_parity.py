@@ -208,6 +208,32 @@ def test_save_load_resumes_bitwise(dem):
             assert np.array_equal(ref[key], got[key]), (prec, key)
 
 
+def test_step_chunks_give_the_same_bits(dem):
+    # The pose of a rotating mesh is computed one step ahead into a buffer of
+    # the step's parity; graphs of 1 and 16 steps, phase-timed steps and a
+    # save/load at an odd step must all see the same poses.
+    for prec in (0, 1):
+        s = scenes.drum_scene(n=1500, seed=4, n_theta=32, n_rings=4, nn_dist=2.3e-3,
+                              radius=0.022)
+        a = dem.Scene.from_dict(s, precision=prec)
+        a.step(77)
+        ref = a.state()
+        b = dem.Scene.from_dict(s, precision=prec)
+        b.step(1)
+        b.step_timed(3)
+        b.step(17)
+        b.step(32)
+        blob = b.save()  # at step 53
+        b.step_timed(1)
+        b.step(23)
+        c = dem.Scene.from_dict(s, precision=prec)
+        c.load(blob)
+        c.step(24)
+        for got in (b.state(), c.state()):
+            for key in ref:
+                assert np.array_equal(ref[key], got[key]), (prec, key)
+
+
 def test_capacity_overflow_is_reported_not_corrupting(dem):
     s = scenes.lattice_box_scene((6, 6, 6), spacing=1.9e-3)
     sc = dem.Scene.from_dict(s, precision=0, max_neighbors=2)

@@ -25,10 +25,15 @@ def test_small_heap_in_both_precisions(repose):
     for runs in out.values():
         for r in runs:
             assert r["status"] == 0 and r["settled"] and r["active"] == 3000
-            # a small heap: flanks well below the large-heap angle, both alike
+            # a small heap: flanks well below the large-heap angle
             assert 20.0 < r["theta"] < 45.0
-            assert abs(r["theta_left"] - r["theta_right"]) < 6.0
+            assert abs(r["theta_left"] - r["theta_right"]) < 10.0
             assert 0.42 < r["packing_core"] < 0.62
+        # the two flanks alike on average (one small heap can lean: flanks of
+        # 28.8 and 36.2 degrees were seen)
+        left = np.mean([r["theta_left"] for r in runs])
+        right = np.mean([r["theta_right"] for r in runs])
+        assert abs(left - right) < 4.0
     # A 3,000-grain heap is chaotic: a rounding-level change moves one
     # realisation's angle by several per cent (29.1 and 27.2 degrees for the
     # same seed), so the precisions are compared on the mean of three seeds.
