@@ -191,7 +191,7 @@ def measured_traffic(n: int, mixed: bool):
     is scaled to n particles (traffic grows in proportion) and reported only
     while the sources are unchanged.
     """
-    name = "k_step_warp_mixed_drum400k.md" if mixed else "k_step_warp_fp64_drum400k.md"
+    name = "k_step_warp_mixed_drum400k.md" if mixed else "k_pairs_gather_fp64_drum400k.md"
     try:
         with open(os.path.join(ROOT, "profiles", name)) as f:
             for line in f:
@@ -271,7 +271,7 @@ def bench_ours(a):
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"],
                 "traffic": measured_traffic(n, prec == dem.DEM_MIXED),
-                "peak_source": peak_src, "kernel": "k_step_warp<MixedPolicy>" if prec else "k_step_warp<Fp64Policy>",
+                "peak_source": peak_src, "kernel": "k_step_warp<MixedPolicy>" if prec else "k_pairs_fp64+k_gather_fp64",
                 "kernel_ms": step_ms, "algorithmic_bytes_per_launch": bytes_launch,
                 "phase_ms_per_step": {"mesh_pose": ph[0] / k_phase, "rebuild": ph[1] / k_phase,
                                       "step": ph[2] / k_phase, "advance": ph[3] / k_phase}}
