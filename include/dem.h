@@ -199,7 +199,10 @@ int dem_synchronize(dem_scene* s);
 
 /* Copy the current state to host arrays in caller order, n_cap rows (see
  * dem_params.n_max); any pointer may be NULL.  Rows of inactive particles
- * hold zeros and the identity orientation.  Synchronizes the stream. */
+ * hold zeros and the identity orientation.  The conversion to absolute
+ * doubles and the reordering run on the device (into a staging buffer the
+ * scene owns); then one copy per array goes to the caller's memory, which
+ * may be pageable or pinned (pinned is faster).  Synchronizes the stream. */
 int dem_read_state(dem_scene* s, double* x, double* v, double* w, double* q);
 
 /* Particle radii in caller order, n_cap rows (0 for inactive rows).

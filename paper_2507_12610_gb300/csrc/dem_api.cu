@@ -140,6 +140,7 @@ struct dem_scene {
   BinBuf bb{};
   MeshDev mesh{};
   double* forces = nullptr;
+  double* export_buf = nullptr;  // [13 n] state read-back staging (caller order)
   Alloc mem;
   // step graphs (1 and kGraphSteps steps) for a start at an even / odd step:
   // each captured step passes its kernels the pose buffers of its parity
@@ -904,6 +905,7 @@ int dem_scene_create(const dem_params* params, const dem_particles* parts, const
   s->bb.tmp_cnt = M.get<uint32_t>(n);
   s->bb.tmp_offs = M.get<uint32_t>(n + 1);
   if (p.record_forces) s->forces = M.get<double>(6 * (size_t)n);
+  s->export_buf = M.get<double>(13 * (size_t)n);
   if (!p.mixed && !fp64_two_sided()) {  // DEM_FP64: one evaluation per pair
     p.pair_res = M.get<unsigned char>((size_t)p.cap * n * pair_result_bytes());
     p.pair_stamp = M.get<uint32_t>((size_t)p.cap * n);
@@ -1109,56 +1111,20 @@ int dem_synchronize(dem_scene* s) {
 
 int dem_read_state(dem_scene* s, double* x, double* v, double* w, double* q) {
   if (!s) return DEM_ERR_INVALID;
-  Ctl c;
-  int rc = read_ctl(s, &c);
-  if (rc != DEM_OK) return rc;
-  HostState h;
-  rc = fetch_state(s, c, h);
-  if (rc != DEM_OK) return rc;
+  // converted and put in caller order on the device, then one copy per array
   const int64_t n = s->n;
-  for (int64_t t = 0; t < n; ++t) {
-    const int64_t i = h.gid[t];
-    const bool inactive = s->p.mixed ? (h.Pm[t].hi.w == 0.f) : (h.Pd[t].w == 0.0);
-    if (inactive) {  // awaiting spawning
-      for (int a = 0; a < 3; ++a) {
-        if (x) x[3 * i + a] = 0.0;
-        if (v) v[3 * i + a] = 0.0;
-        if (w) w[3 * i + a] = 0.0;
-      }
-      if (q) q[4 * i] = 1.0, q[4 * i + 1] = q[4 * i + 2] = q[4 * i + 3] = 0.0;
-      continue;
-    }
-    if (s->p.mixed) {
-      const F8 &P = h.Pm[t], &V = h.Vm[t], &W = h.Wm[t], &Q = h.Qm[t];
-      if (x) {
-        x[3 * i] = s->p.origin[0] + ((double)P.hi.x + (double)P.lo.x);
-        x[3 * i + 1] = s->p.origin[1] + ((double)P.hi.y + (double)P.lo.y);
-        x[3 * i + 2] = s->p.origin[2] + ((double)P.hi.z + (double)P.lo.z);
-      }
-      if (v) {
-        v[3 * i] = (double)V.hi.x + (double)V.lo.x;
-        v[3 * i + 1] = (double)V.hi.y + (double)V.lo.y;
-        v[3 * i + 2] = (double)V.hi.z + (double)V.lo.z;
-      }
-      if (w) {
-        w[3 * i] = (double)W.hi.x + (double)W.lo.x;
-        w[3 * i + 1] = (double)W.hi.y + (double)W.lo.y;
-        w[3 * i + 2] = (double)W.hi.z + (double)W.lo.z;
-      }
-      if (q) {
-        q[4 * i] = (double)Q.hi.x + (double)Q.lo.x;
-        q[4 * i + 1] = (double)Q.hi.y + (double)Q.lo.y;
-        q[4 * i + 2] = (double)Q.hi.z + (double)Q.lo.z;
-        q[4 * i + 3] = (double)Q.hi.w + (double)Q.lo.w;
-      }
-    } else {
-      const D4 &P = h.Pd[t], &V = h.Vd[t], &W = h.Wd[t], &Q = h.Qd[t];
-      if (x) x[3 * i] = P.x, x[3 * i + 1] = P.y, x[3 * i + 2] = P.z;
-      if (v) v[3 * i] = V.x, v[3 * i + 1] = V.y, v[3 * i + 2] = V.z;
-      if (w) w[3 * i] = W.x, w[3 * i + 1] = W.y, w[3 * i + 2] = W.z;
-      if (q) q[4 * i] = Q.x, q[4 * i + 1] = Q.y, q[4 * i + 2] = Q.z, q[4 * i + 3] = Q.w;
-    }
+  launch_export_state(s->stream, s->ctl, s->p, s->sb, s->L, n, s->export_buf);
+  DEM_TRY(cudaGetLastError());
+  double* const dst[4] = {x, v, w, q};
+  for (int k = 0; k < 4; ++k) {
+    if (!dst[k]) continue;
+    const size_t off = (size_t)(3 * k) * n, len = (size_t)(k == 3 ? 4 : 3) * n;
+    DEM_TRY(cudaMemcpyAsync(dst[k], s->export_buf + off, len * sizeof(double),
+                            cudaMemcpyDeviceToHost, s->stream));
   }
+  Ctl c;
+  const int rc = read_ctl(s, &c);
+  if (rc != DEM_OK) return rc;
   return (int)c.status;
 }
 

@@ -257,6 +257,10 @@ void launch_rebuild(cudaStream_t st, Ctl* ctl, const Params& p, StateBufs sb, Li
 void launch_step(cudaStream_t st, Ctl* ctl, const Params& p, StateBufs sb, Lists L,
                  MeshDev mesh, double* forces);
 void launch_advance(cudaStream_t st, Ctl* ctl, const Params& p);
+// The current state in caller order as doubles: x[n][3], v[n][3], w[n][3],
+// q[n][4] one after another in `out` (13 n doubles, device memory).
+void launch_export_state(cudaStream_t st, const Ctl* ctl, const Params& p, StateBufs sb,
+                         Lists L, int64_t n, double* out);
 // Sets ctl->rot_c / rot_s for the step in the control block.
 void launch_set_pose(cudaStream_t st, Ctl* ctl, const Params& p);
 // Sets a graph IF-condition from ctl->rebuild (inside a captured graph).
