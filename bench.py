@@ -174,8 +174,9 @@ def kernel_sources_sha1() -> str:
     matches."""
     import hashlib
     d = os.path.join(ROOT, "paper_2507_12610_gb300", "csrc")
-    files = ["dem_step.cu", "dem_step_fp64.cu", "dem_step_warp.cuh", "dem_step_common.cuh",
-             "dem_law.cuh", "dem_geom.cuh", "dem_math.cuh", "dem_internal.cuh"]
+    files = ["dem_step.cu", "dem_step_fp64.cu", "dem_step_warp.cuh", "dem_step_pairs.cuh",
+             "dem_step_common.cuh", "dem_law.cuh", "dem_geom.cuh", "dem_math.cuh",
+             "dem_internal.cuh"]
     h = hashlib.sha1()
     for f in files:
         with open(os.path.join(d, f), "rb") as fh:
@@ -271,7 +272,7 @@ def bench_ours(a):
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"],
                 "traffic": measured_traffic(n, prec == dem.DEM_MIXED),
-                "peak_source": peak_src, "kernel": "k_step_warp<MixedPolicy>" if prec else "k_pairs_fp64+k_gather_fp64",
+                "peak_source": peak_src, "kernel": "k_step_warp<MixedPolicy>" if prec else "k_pairs+k_gather<Fp64Policy>",
                 "kernel_ms": step_ms, "algorithmic_bytes_per_launch": bytes_launch,
                 "phase_ms_per_step": {"mesh_pose": ph[0] / k_phase, "rebuild": ph[1] / k_phase,
                                       "step": ph[2] / k_phase, "advance": ph[3] / k_phase}}

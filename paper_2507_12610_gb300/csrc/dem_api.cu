@@ -545,6 +545,8 @@ int clear_histories(dem_scene* s) {
     DEM_TRY(cudaMemset(lb.hpp, 0xff, (size_t)s->p.cap * s->n * s->hist_bytes));
     if (lb.hpm) DEM_TRY(cudaMemset(lb.hpm, 0xff, (size_t)s->p.capm * s->n * s->hist_bytes));
   }
+  // touch masks start clear (the gather clears them again after every step)
+  if (s->p.pair_touch) DEM_TRY(cudaMemset(s->p.pair_touch, 0, (size_t)s->n * 8));
   return DEM_OK;
 }
 
@@ -888,7 +890,10 @@ int dem_scene_create(const dem_params* params, const dem_particles* parts, const
     lb.offs = M.get<uint32_t>(n + 1);
     lb.nbr = M.get<uint32_t>((size_t)p.cap * n);
     lb.hpp = M.get<unsigned char>((size_t)p.cap * n * s->hist_bytes);
-    if (!p.mixed) lb.mir = M.get<uint32_t>((size_t)p.cap * n);
+    if (!p.mixed && !fp64_two_sided()) {
+      lb.mir = M.get<uint32_t>((size_t)p.cap * n);
+      lb.back = M.get<uint8_t>((size_t)p.cap * n);
+    }
     if (has_mesh) {
       lb.tric = M.get<uint32_t>((size_t)p.capm * n);
       lb.hpm = M.get<unsigned char>((size_t)p.capm * n * s->hist_bytes);
@@ -908,7 +913,7 @@ int dem_scene_create(const dem_params* params, const dem_particles* parts, const
   s->export_buf = M.get<double>(13 * (size_t)n);
   if (!p.mixed && !fp64_two_sided()) {  // DEM_FP64: one evaluation per pair
     p.pair_res = M.get<unsigned char>((size_t)p.cap * n * pair_result_bytes());
-    p.pair_stamp = M.get<uint32_t>((size_t)p.cap * n);
+    p.pair_touch = M.get<unsigned long long>((size_t)n);
   }
   if (has_mesh) {
     s->bb.tcell_count = M.get<uint32_t>(ncells);

@@ -86,8 +86,9 @@ struct Params {
   // index of a particle is in its W record (mixed: lo.w as int bits; FP64: w)
   int32_t step_warps;       // warps per block of the step kernel (4 or 8)
   // DEM_FP64 one-evaluation-per-pair scheme (NULL: both sides evaluate)
-  void* pair_res;           // [list capacity] per-entry pair results
-  uint32_t* pair_stamp;     // [list capacity] step stamp of each result
+  void* pair_res;           // [list capacity] per-entry pair results (DEM_FP64: one
+                            // evaluation per pair)
+  unsigned long long* pair_touch;  // [n] bit k: list entry k touched in this step
   int32_t n_mat;
   const float4* mat_f;      // [n_mat] mu_s, mu_r, mu_t, 0
   const D4* mat_d;          // [n_mat] mu_s, mu_r, mu_t, 0
@@ -146,7 +147,9 @@ struct ListBuf {
   uint32_t* tric;   // [capm][n] candidate triangles, ascending
   void* hpm;        // [capm][n] triangle history
   uint32_t* mir;    // [offs[n]] for an entry whose partner has the lower caller index,
-                    // the partner's entry for the same pair (DEM_FP64 only)
+                    // the partner's entry for the same pair (one evaluation per pair)
+  uint8_t* back;    // [offs[n]] for an entry whose partner has the higher caller index,
+                    // the index of this particle in the partner's list
 };
 
 // Mesh elements (Sec. 3.3): triangles first, then points, segments and
@@ -217,7 +220,7 @@ struct Lists {
 __device__ __forceinline__ void* buf_of(void* const (&a)[2], uint32_t b) {
   return b ? a[1] : a[0];
 }
-size_t pair_result_bytes();
+size_t pair_result_bytes();  // bytes of one entry's DEM_FP64 pair result
 
 // The mesh with the pose arrays of step `step` (even or odd buffers).
 inline MeshDev mesh_at(const MeshDev& m, int64_t step) {
@@ -242,6 +245,7 @@ __device__ __forceinline__ ListBuf list_of(const Lists& L, uint32_t b) {
   r.tric = b ? L.b[1].tric : L.b[0].tric;
   r.hpm = b ? L.b[1].hpm : L.b[0].hpm;
   r.mir = b ? L.b[1].mir : L.b[0].mir;
+  r.back = b ? L.b[1].back : L.b[0].back;
   return r;
 }
 #endif

@@ -431,7 +431,8 @@ inline unsigned blocks_for(int64_t n, int threads) {
 
 // For every entry whose partner u has the lower caller index, the index of
 // u's entry for the same pair: u's list is sorted by partner caller index, so
-// a binary search over its upper entries finds this particle.
+// a binary search over its upper entries finds this particle.  That entry of
+// u gets, in return, this entry's index k in this particle's list.
 __global__ void __launch_bounds__(128)
 k_mirror(Ctl* ctl, Params p, Lists L) {
   if (!rebuilding(ctl)) return;
@@ -452,6 +453,7 @@ k_mirror(Ctl* ctl, Params p, Lists L) {
       else hi = mid;
     }
     ln.mir[off + k] = lo;
+    ln.back[lo] = (uint8_t)k;
   }
 }
 

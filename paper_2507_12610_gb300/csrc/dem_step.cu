@@ -305,6 +305,24 @@ struct MixedPolicy {
                                               const F8& Wi, const F8& Wj, HistM& h,
                                               uint32_t stamp_now, uint32_t stamp_new,
                                               float c6[6]) {
+    LawOut<float> o;
+    if (!pair_law(p, Pi, Pj, Vi, Vj, Wi, Wj, h, stamp_now, stamp_new, o)) return false;
+    if (t_is_i) {
+      c6[0] = o.f.x; c6[1] = o.f.y; c6[2] = o.f.z;
+      c6[3] = o.ti.x; c6[4] = o.ti.y; c6[5] = o.ti.z;
+    } else {
+      c6[0] = -o.f.x; c6[1] = -o.f.y; c6[2] = -o.f.z;
+      c6[3] = o.tj.x; c6[4] = o.tj.y; c6[5] = o.tj.z;
+    }
+    return true;
+  }
+
+  // The law of a canonical pair (i, j): if it touches, updates the history
+  // and returns the force on i and the torques on i and j.
+  static __device__ __forceinline__ bool pair_law(const Params& p, const F8& Pi, const F8& Pj,
+                                                  const F8& Vi, const F8& Vj, const F8& Wi,
+                                                  const F8& Wj, HistM& h, uint32_t stamp_now,
+                                                  uint32_t stamp_new, LawOut<float>& o) {
     Geo g;
     if (!touch(p, Pi, Pj, g)) return false;
     LawConst<float> cpp{p.f_Es_pp, p.f_Gs_pp, p.f_beta, p.f_mu_s, p.f_mu_r, p.f_mu_t, p.f_dt};
@@ -325,20 +343,12 @@ struct MixedPolicy {
       ur = mk(h.ur[0], h.ur[1], h.ur[2]);
       ut = h.ut;
     }
-    const LawOut<float> o =
-        contact_law(cpp, g.n, g.delta, Rs, ms, ri, rj, 1.f / ri + 1.f / rj, diff3(Vi, Vj),
+    o = contact_law(cpp, g.n, g.delta, Rs, ms, ri, rj, 1.f / ri + 1.f / rj, diff3(Vi, Vj),
                     ri * sum3(Wi) + rj * sum3(Wj), diff3(Wi, Wj), us, ur, ut);
     h.us[0] = us.x; h.us[1] = us.y; h.us[2] = us.z;
     h.ur[0] = ur.x; h.ur[1] = ur.y; h.ur[2] = ur.z;
     h.ut = ut;
     h.stamp = stamp_new;
-    if (t_is_i) {
-      c6[0] = o.f.x; c6[1] = o.f.y; c6[2] = o.f.z;
-      c6[3] = o.ti.x; c6[4] = o.ti.y; c6[5] = o.ti.z;
-    } else {
-      c6[0] = -o.f.x; c6[1] = -o.f.y; c6[2] = -o.f.z;
-      c6[3] = o.tj.x; c6[4] = o.tj.y; c6[5] = o.tj.z;
-    }
     return true;
   }
 

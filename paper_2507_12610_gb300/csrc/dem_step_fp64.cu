@@ -10,6 +10,7 @@
 #include "dem_law.cuh"
 #include "dem_math.cuh"
 #include "dem_step_common.cuh"
+#include "dem_step_pairs.cuh"
 #include "dem_step_warp.cuh"
 
 namespace dem {
@@ -249,181 +250,15 @@ struct Fp64Policy {
 
 }  // namespace
 
-namespace {
-
-// ---- one evaluation per pair ---------------------------------------------------
-//
-// The FP64 step is bound by the FP64 pipe, so each touching pair is evaluated
-// once, by its lower-caller-index particle i (its "upper" entries, partner
-// index above its own), which writes the force on i and both torques to the
-// entry's result record.  A second kernel then sums, for every particle, its
-// lower entries (through the mirror index: the partner's entry for this pair;
-// force negated, torque on j) and its upper entries (force, torque on i) in
-// list order, i.e. in ascending partner caller index -- the same values in
-// the same order as evaluating the pair from both sides, so the results are
-// bitwise those of that scheme.  History lives at the upper entries only.
-
-struct PairOut {  // a pair's result in canonical orientation (80 bytes)
-  double f[3];   // force on i
-  double ti[3];  // torque on i
-  double tj[3];  // torque on j
-  double pad;
-};
-
-constexpr int kPairWarps = 4;
-
-// Phase A / B of the warp kernel (see dem_step_warp.cuh) over the warp's
-// upper entries only; each touching pair's result goes to its entry.
-__global__ void __launch_bounds__(32 * kPairWarps, Fp64Policy::kMinBlocks)
-k_pairs_fp64(Ctl* ctl, Params p, StateBufs sb, Lists L, PairOut* res, uint32_t* rstamp) {
-  __shared__ uint32_t seg_s[kPairWarps][33];
-  __shared__ uint32_t off_s[kPairWarps][32];
-  __shared__ uint32_t qent_s[kPairWarps][kQueueMax];
-  __shared__ uint32_t qslot_s[kPairWarps][kQueueMax];
-  __shared__ uint8_t qlane_s[kPairWarps][kQueueMax];
-  if (ctl->status) return;
-  const unsigned full = 0xffffffffu;
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  uint32_t* seg = seg_s[wib];
-  uint32_t* offw = off_s[wib];
-  uint32_t* qent = qent_s[wib];
-  uint32_t* qslot = qslot_s[wib];
-  uint8_t* qlane = qlane_s[wib];
-  const int n = p.n;
-  const int w0 = (blockIdx.x * kPairWarps + wib) * 32;
-  const int t = w0 + lane;
-  const bool valid = t < n;
-  const uint32_t ph = ctl->phase & 1u, lph = ctl->lphase & 1u;
-  const uint32_t stamp_now = (uint32_t)ctl->step, stamp_new = stamp_now + 1u;
-  const D4* P = static_cast<const D4*>(buf_of(sb.P, ph));
-  const D4* V = static_cast<const D4*>(buf_of(sb.V, ph));
-  const D4* W = static_cast<const D4*>(buf_of(sb.W, ph));
-  const ListBuf lb = list_of(L, lph);
-  HistD* Hh = static_cast<HistD*>(lb.hpp);
-  const uint32_t meta = valid ? lb.meta[t] : 0u;
-  const uint32_t nn = meta & 0xffu, nlow = (meta >> 8) & 0xffu;
-  const uint32_t incl = warp_incl_scan(nn - nlow);
-  seg[lane + 1] = incl;
-  if (lane == 0) seg[0] = 0;
-  offw[lane] = valid ? lb.offs[t] + nlow : 0u;
-  const uint32_t Eu = __shfl_sync(full, incl, 31);
-  __syncwarp();
-  uint32_t npair = 0;
-  uint32_t e0 = 0;
-  while (e0 < Eu) {
-    // A: pre-test, queue the candidates (entry, partner slot, owner lane)
-    uint32_t qn = 0;
-    for (; e0 < Eu && qn + 32 <= (uint32_t)kQueueMax; e0 += 32) {
-      const uint32_t e = e0 + lane;
-      bool hit = false;
-      uint32_t ent = 0, u = 0;
-      int tl = 0;
-      if (e < Eu) {
-        int lo = 0;
-#pragma unroll
-        for (int step = 16; step > 0; step >>= 1)
-          if (seg[lo + step] <= e) lo += step;
-        tl = lo;
-        ent = offw[tl] + (e - seg[tl]);
-        u = lb.nbr[ent];
-        hit = Fp64Policy::near(P[w0 + tl], P[u]);
-      }
-      const unsigned m = __ballot_sync(full, hit);
-      if (hit) {
-        const uint32_t pos = qn + __popc(m & ((1u << lane) - 1u));
-        qent[pos] = ent;
-        qslot[pos] = u;
-        qlane[pos] = (uint8_t)tl;
-      }
-      qn += __popc(m);
-    }
-    __syncwarp();
-    // B: the law for 32 queued pairs at a time, results to their entries
-    for (uint32_t i0 = 0; i0 < qn; i0 += 32) {
-      const uint32_t i = i0 + lane;
-      if (i < qn) {
-        const uint32_t ent = qent[i], u = qslot[i];
-        const int tl = qlane[i];
-        HistD h = Hh[ent];
-        LawOut<double> o;
-        if (Fp64Policy::pair_law(p, P[w0 + tl], P[u], V[w0 + tl], V[u], W[w0 + tl], W[u], h,
-                                 stamp_now, stamp_new, o)) {
-          Hh[ent] = h;
-          PairOut r;
-          r.f[0] = o.f.x; r.f[1] = o.f.y; r.f[2] = o.f.z;
-          r.ti[0] = o.ti.x; r.ti[1] = o.ti.y; r.ti[2] = o.ti.z;
-          r.tj[0] = o.tj.x; r.tj[1] = o.tj.y; r.tj[2] = o.tj.z;
-          r.pad = 0.0;
-          res[ent] = r;
-          rstamp[ent] = stamp_new;
-          npair += 2;  // two directed entries, as the stats count them
-        }
-      }
-    }
-    __syncwarp();
-  }
-  count_and_flag(ctl, npair, 0u, false, false);
-}
-
-// Per particle: the pair sums in list order (lower entries through the mirror
-// index, then upper entries), then mesh contacts and integration.
-__global__ void __launch_bounds__(128, Fp64Policy::kMinBlocks)
-k_gather_fp64(Ctl* ctl, Params p, StateBufs sb, Lists L, MeshDev mesh, const PairOut* res,
-              const uint32_t* rstamp, double* forces) {
-  if (ctl->status) return;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool valid = t < p.n;
-  const uint32_t ph = ctl->phase & 1u, lph = ctl->lphase & 1u;
-  const uint32_t stamp_now = (uint32_t)ctl->step, stamp_new = stamp_now + 1u;
-  const ListBuf lb = list_of(L, lph);
-  uint32_t nmesh = 0;
-  bool disp = false, bad = false;
-  if (valid) {
-    const D4* P = static_cast<const D4*>(buf_of(sb.P, ph));
-    const D4* V = static_cast<const D4*>(buf_of(sb.V, ph));
-    const D4* W = static_cast<const D4*>(buf_of(sb.W, ph));
-    const uint32_t meta = lb.meta[t];
-    const uint32_t nn = meta & 0xffu, nlow = (meta >> 8) & 0xffu;
-    const uint32_t off = lb.offs[t];
-    Fp64Policy::Acc acc;
-    acc.zero();
-    double c6[6];
-    for (uint32_t k = 0; k < nn; ++k) {
-      if (k < nlow) {
-        const uint32_t e2 = lb.mir[off + k];
-        if (rstamp[e2] != stamp_new) continue;
-        const PairOut& r = res[e2];
-        c6[0] = -r.f[0]; c6[1] = -r.f[1]; c6[2] = -r.f[2];
-        c6[3] = r.tj[0]; c6[4] = r.tj[1]; c6[5] = r.tj[2];
-      } else {
-        if (rstamp[off + k] != stamp_new) continue;
-        const PairOut& r = res[off + k];
-        c6[0] = r.f[0]; c6[1] = r.f[1]; c6[2] = r.f[2];
-        c6[3] = r.ti[0]; c6[4] = r.ti[1]; c6[5] = r.ti[2];
-      }
-      acc.add(c6);
-    }
-    Fp64Policy::finish(p, sb, ph, lb, mesh, t, (meta >> 16) & 0xffu, P[t], V[t], W[t], acc,
-                       stamp_now, stamp_new, forces, nmesh, disp, bad);
-  }
-  count_and_flag(ctl, 0u, nmesh, disp, bad);
-}
-
-}  // namespace
-
 void launch_step_fp64(cudaStream_t st, Ctl* ctl, const Params& p, StateBufs sb, Lists L,
                       MeshDev mesh, double* forces) {
-  if (!p.pair_res) {  // both sides evaluate each pair (the one-kernel scheme)
+  if (p.pair_res)  // one evaluation per pair: the FP64 pipe bounds this step
+    launch_step_pairs<Fp64Policy, Fp64Policy::kMinBlocks, Fp64Policy::kMinBlocks>(
+        st, ctl, p, sb, L, mesh, forces);
+  else  // both sides evaluate each pair (one kernel)
     launch_step_warp<Fp64Policy>(st, ctl, p, sb, L, mesh, forces);
-    return;
-  }
-  PairOut* res = static_cast<PairOut*>(p.pair_res);
-  k_pairs_fp64<<<(unsigned)((p.n + 32 * kPairWarps - 1) / (32 * kPairWarps)), 32 * kPairWarps,
-                 0, st>>>(ctl, p, sb, L, res, p.pair_stamp);
-  k_gather_fp64<<<(unsigned)((p.n + 127) / 128), 128, 0, st>>>(ctl, p, sb, L, mesh, res,
-                                                                p.pair_stamp, forces);
 }
 
-size_t pair_result_bytes() { return sizeof(PairOut); }
+size_t pair_result_bytes() { return sizeof(PairOut<double>); }
 
 }  // namespace dem

@@ -283,9 +283,10 @@ def test_momentum_conserved_at_scale(dem):
 
 
 def test_fp64_one_evaluation_per_pair_is_bitwise_the_two_sided_scheme(dem, monkeypatch):
-    # DEM_FP64 evaluates each pair once and hands the result to the partner;
-    # the environment switch selects the scheme that evaluates it from both
-    # sides.  Same values, summed in the same order: the same bits.
+    # Each pair is evaluated once and its result handed to the partner; the
+    # environment switch selects the scheme that evaluates it from both sides.
+    # Same values, summed in the same order: in DEM_FP64 (no contraction) the
+    # same bits.
     s = SCENES["drum_small"]()
     out = []
     for two in ("0", "1"):
