@@ -63,6 +63,27 @@ def repose_angle(x, z, R, lo, hi, width, lo_frac=0.2, hi_frac=0.8):
     return out
 
 
+def drum_surface_angle(x, R, drum_radius, drum_length, width, band=0.5, section=0.5):
+    """Free-surface angle of the bed in a drum turning about the x axis.
+
+    The spheres of the middle `section` of the drum's length (away from the
+    end caps) are projected onto the y-z cross-section; the surface profile
+    is the highest sphere top (z + R) per bin of the given width along y, and
+    a least-squares line through the bins with |y| < band * drum_radius
+    (away from the shell) gives its slope.  Returns the angle to the
+    horizontal in degrees (positive: the surface rises towards +y).
+    """
+    x = np.asarray(x)
+    sel = np.abs(x[:, 0]) < 0.5 * section * drum_length
+    half = band * drum_radius
+    yc, h = surface_profile(x[sel, 1], x[sel, 2], np.asarray(R)[sel], -half, half, width)
+    good = np.isfinite(h)
+    if good.sum() < 4:
+        raise ValueError("no free surface")
+    slope = np.polyfit(yc[good], h[good], 1)[0]
+    return math.degrees(math.atan(slope))
+
+
 def packing_fraction(x, R, box_lo, box_hi):
     """Solid fraction of an axis-aligned box: volume of the spheres whose
     centres lie inside it over its volume (spheres cut by the box faces are
