@@ -352,16 +352,82 @@ struct MixedPolicy {
     return true;
   }
 
-  // Triangle contacts and integration of particle slot t.
+  // Contact of particle slot t with its m-th element candidate: the FP32
+  // closest point as a pre-filter and to pick the nearest feature, then the
+  // overlap in compensated FP32 (an element is large compared with the
+  // overlap).  If they touch, updates the history and writes the force and
+  // torque on the particle to c6.
+  static __device__ __forceinline__ bool mesh_contact(const Params& p, const MeshDev& mesh,
+                                                      const ListBuf& lb, int t, int m,
+                                                      const F8& Pt, const F8& Vt, const F8& Wt,
+                                                      uint32_t stamp_now, uint32_t stamp_new,
+                                                      float c6[6]) {
+    const int n = p.n;
+    const float Rt = Pt.hi.w + Pt.lo.w;
+    const uint32_t kt = lb.tric[(size_t)m * n + t];
+    const V3<float> qf = sum3(Pt);
+    const float4 Af = mesh.curf[4 * kt], Bf = mesh.curf[4 * kt + 1],
+                 Cf = mesh.curf[4 * kt + 2], Df = mesh.curf[4 * kt + 3];
+    const int nvk = (int)Af.w;
+    int feat;
+    const V3<float> yf = closest_point_element(qf, hi3(Af), hi3(Bf), hi3(Cf), hi3(Df), nvk, feat);
+    const V3<float> df = qf - yf;
+    const float4 Al = mesh.curl[4 * kt], Bl = mesh.curl[4 * kt + 1];
+    const float reachf = Rt + Al.w + p.mesh_prefilter;
+    if (dot(df, df) > reachf * reachf) return false;
+    float delta;
+    V3<float> nh;
+    if (!mesh_gap(mesh, kt, feat, Pt, Al, Bl, delta, nh)) return false;
+    LawConst<float> cpw{p.f_Es_pw, p.f_Gs_pw, p.f_beta, p.f_mu_s, p.f_mu_r, p.f_mu_t, p.f_dt};
+    if (p.n_mat > 0) {  // the particle's material
+      const float4 a = p.mat_f[__float_as_int(Wt.lo.w)];
+      cpw.mu_s = a.x;
+      cpw.mu_r = a.y;
+      cpw.mu_t = a.z;
+    }
+    const V3<float> Om = mk(p.f_omega[0], p.f_omega[1], p.f_omega[2]);
+    // particle centre relative to the rotation axis point, accurately
+    const V3<float> rc = mk((Pt.hi.x - p.center_hi[0]) + (Pt.lo.x - p.center_lo[0]),
+                            (Pt.hi.y - p.center_hi[1]) + (Pt.lo.y - p.center_lo[1]),
+                            (Pt.hi.z - p.center_hi[2]) + (Pt.lo.z - p.center_lo[2]));
+    const float ri = Rt - 0.5f * delta;
+    const V3<float> vw = cross(Om, rc - ri * nh);
+    HistM* hp = &static_cast<HistM*>(lb.hpm)[(size_t)m * n + t];
+    const HistM h = *hp;
+    V3<float> us = mk(0.f, 0.f, 0.f), ur = us;
+    float ut = 0.f;
+    if (h.stamp == stamp_now) {
+      us = mk(h.us[0], h.us[1], h.us[2]);
+      ur = mk(h.ur[0], h.ur[1], h.ur[2]);
+      ut = h.ut;
+    }
+    const V3<float> dv = mk((Vt.hi.x - vw.x) + Vt.lo.x, (Vt.hi.y - vw.y) + Vt.lo.y,
+                            (Vt.hi.z - vw.z) + Vt.lo.z);
+    const V3<float> om = mk((Wt.hi.x - Om.x) + Wt.lo.x, (Wt.hi.y - Om.y) + Wt.lo.y,
+                            (Wt.hi.z - Om.z) + Wt.lo.z);
+    const LawOut<float> o = contact_law(cpw, nh, delta, Rt, Vt.hi.w, ri, 0.f, 1.f / ri, dv,
+                                        ri * sum3(Wt), om, us, ur, ut);
+    HistM hn;
+    hn.us[0] = us.x; hn.us[1] = us.y; hn.us[2] = us.z;
+    hn.ur[0] = ur.x; hn.ur[1] = ur.y; hn.ur[2] = ur.z;
+    hn.ut = ut;
+    hn.stamp = stamp_new;
+    *hp = hn;
+    c6[0] = o.f.x; c6[1] = o.f.y; c6[2] = o.f.z;
+    c6[3] = o.ti.x; c6[4] = o.ti.y; c6[5] = o.ti.z;
+    return true;
+  }
+
+  // Element contacts (unless the caller took them already: with_mesh false)
+  // and integration of particle slot t.
   static __device__ __forceinline__ void finish(const Params& p, const StateBufs& sb,
                                                 uint32_t ph, const ListBuf& lb,
                                                 const MeshDev& mesh, int t, uint32_t ntc_u,
-                                                const F8& Pt, const F8& Vt, const F8& Wt,
-                                                Acc& sums, uint32_t stamp_now, uint32_t stamp_new,
-                                                double* forces, uint32_t& nmesh, bool& disp,
-                                                bool& bad) {
-    const int n = p.n;
-    const int ntc = (int)ntc_u;
+                                                bool with_mesh, const F8& Pt, const F8& Vt,
+                                                const F8& Wt, Acc& sums, uint32_t stamp_now,
+                                                uint32_t stamp_new, double* forces,
+                                                uint32_t& nmesh, bool& disp, bool& bad) {
+    const int ntc = with_mesh ? (int)ntc_u : 0;
     const F8* Q = static_cast<const F8*>(buf_of(sb.Q, ph));
     const float Rt = Pt.hi.w + Pt.lo.w;
     if (Rt == 0.f) {  // inactive (awaiting spawning): carried over unchanged
@@ -375,67 +441,11 @@ struct MixedPolicy {
     }
     Acc3& F = sums.F;
     Acc3& T = sums.T;
-    // particle-element contacts: FP32 closest point as a pre-filter and to
-    // pick the nearest feature, then the overlap of the near candidates in
-    // compensated FP32 (an element is large compared with the overlap)
-    if (ntc > 0) {
-      LawConst<float> cpw{p.f_Es_pw, p.f_Gs_pw, p.f_beta, p.f_mu_s, p.f_mu_r, p.f_mu_t,
-                          p.f_dt};
-      if (p.n_mat > 0) {  // the particle's material
-        const float4 a = p.mat_f[__float_as_int(Wt.lo.w)];
-        cpw.mu_s = a.x;
-        cpw.mu_r = a.y;
-        cpw.mu_t = a.z;
-      }
-      HistM* hpm = static_cast<HistM*>(lb.hpm);
-      const V3<float> qf = sum3(Pt);
-      const V3<float> Om = mk(p.f_omega[0], p.f_omega[1], p.f_omega[2]);
-      // particle centre relative to the rotation axis point, accurately
-      const V3<float> rc = mk((Pt.hi.x - p.center_hi[0]) + (Pt.lo.x - p.center_lo[0]),
-                              (Pt.hi.y - p.center_hi[1]) + (Pt.lo.y - p.center_lo[1]),
-                              (Pt.hi.z - p.center_hi[2]) + (Pt.lo.z - p.center_lo[2]));
-      for (int m = 0; m < ntc; ++m) {
-        const uint32_t kt = lb.tric[(size_t)m * n + t];
-        const float4 Af = mesh.curf[4 * kt], Bf = mesh.curf[4 * kt + 1],
-                     Cf = mesh.curf[4 * kt + 2], Df = mesh.curf[4 * kt + 3];
-        const int nvk = (int)Af.w;
-        int feat;
-        const V3<float> yf =
-            closest_point_element(qf, hi3(Af), hi3(Bf), hi3(Cf), hi3(Df), nvk, feat);
-        const V3<float> df = qf - yf;
-        const float4 Al = mesh.curl[4 * kt], Bl = mesh.curl[4 * kt + 1];
-        const float reachf = Rt + Al.w + p.mesh_prefilter;
-        if (dot(df, df) > reachf * reachf) continue;
-        float delta;
-        V3<float> nh;
-        if (!mesh_gap(mesh, kt, feat, Pt, Al, Bl, delta, nh)) continue;
-        const float ri = Rt - 0.5f * delta;
-        const V3<float> vw = cross(Om, rc - ri * nh);
-        HistM* hp = &hpm[(size_t)m * n + t];
-        const HistM h = *hp;
-        V3<float> us = mk(0.f, 0.f, 0.f), ur = us;
-        float ut = 0.f;
-        if (h.stamp == stamp_now) {
-          us = mk(h.us[0], h.us[1], h.us[2]);
-          ur = mk(h.ur[0], h.ur[1], h.ur[2]);
-          ut = h.ut;
-        }
-        const V3<float> dv = mk((Vt.hi.x - vw.x) + Vt.lo.x, (Vt.hi.y - vw.y) + Vt.lo.y,
-                                (Vt.hi.z - vw.z) + Vt.lo.z);
-        const V3<float> om = mk((Wt.hi.x - Om.x) + Wt.lo.x, (Wt.hi.y - Om.y) + Wt.lo.y,
-                                (Wt.hi.z - Om.z) + Wt.lo.z);
-        const LawOut<float> o = contact_law(cpw, nh, delta, Rt, Vt.hi.w, ri, 0.f, 1.f / ri, dv,
-                                            ri * sum3(Wt), om, us, ur, ut);
-        HistM hn;
-        hn.us[0] = us.x; hn.us[1] = us.y; hn.us[2] = us.z;
-        hn.ur[0] = ur.x; hn.ur[1] = ur.y; hn.ur[2] = ur.z;
-        hn.ut = ut;
-        hn.stamp = stamp_new;
-        *hp = hn;
-        F.add(o.f);
-        T.add(o.ti);
-        ++nmesh;
-      }
+    for (int m = 0; m < ntc; ++m) {
+      float c6[6];
+      if (!mesh_contact(p, mesh, lb, t, m, Pt, Vt, Wt, stamp_now, stamp_new, c6)) continue;
+      sums.add(c6);
+      ++nmesh;
     }
     // semi-implicit Euler + SPIRAL with compensated (hi, lo) state
     const float mass = Vt.hi.w;

@@ -123,15 +123,71 @@ struct Fp64Policy {
     return true;
   }
 
+  // Contact of particle slot t with its m-th element candidate (Sec. 2.2
+  // walls, Sec. 3.3 elements): if they touch, updates the history and writes
+  // the force and torque on the particle to c6.
+  static __device__ __forceinline__ bool mesh_contact(const Params& p, const MeshDev& mesh,
+                                                      const ListBuf& lb, int t, int m,
+                                                      const D4& Pt, const D4& Vt, const D4& Wt,
+                                                      uint32_t stamp_now, uint32_t stamp_new,
+                                                      double c6[6]) {
+    const int n = p.n;
+    const uint32_t kt = lb.tric[(size_t)m * n + t];
+    const V3<double> x = xyz(Pt);
+    const D4 A = mesh.cur[4 * kt], B = mesh.cur[4 * kt + 1], C = mesh.cur[4 * kt + 2],
+             D = mesh.cur[4 * kt + 3];
+    const int nvk = (int)mesh.curf[4 * kt].w;
+    const V3<double> pc = closest_point_element(x, xyz(A), xyz(B), xyz(C), xyz(D), nvk);
+    const V3<double> d = x - pc;
+    const double dist = sqrt(dot(d, d));
+    const double delta = Pt.w + A.w - dist;
+    if (delta < 0.0 || !(dist > 0.0)) return false;
+    LawConst<double> cpw{p.Es_pw, p.Gs_pw, p.beta, p.mu_s, p.mu_r, p.mu_t, p.dt};
+    if (p.n_mat > 0) {  // the particle's material
+      const D4 a = p.mat_d[(int)Wt.w];
+      cpw.mu_s = a.x;
+      cpw.mu_r = a.y;
+      cpw.mu_t = a.z;
+    }
+    const V3<double> Om = mk(p.mesh_omega[0], p.mesh_omega[1], p.mesh_omega[2]);
+    const V3<double> ctr = mk(p.mesh_center[0], p.mesh_center[1], p.mesh_center[2]);
+    const V3<double> nh = (1.0 / dist) * d;
+    const double ri = Pt.w - delta / 2.0;
+    const V3<double> xc = x - ri * nh;
+    const V3<double> vw = cross(Om, xc - ctr);
+    HistD* hp = &static_cast<HistD*>(lb.hpm)[(size_t)m * n + t];
+    const HistD h = *hp;
+    V3<double> us = mk(0.0, 0.0, 0.0), ur = us;
+    double ut = 0.0;
+    if (h.stamp == stamp_now) {
+      us = mk(h.us[0], h.us[1], h.us[2]);
+      ur = mk(h.ur[0], h.ur[1], h.ur[2]);
+      ut = h.ut;
+    }
+    const LawOut<double> o = contact_law(cpw, nh, delta, Pt.w, Vt.w, ri, 0.0, 1.0 / ri,
+                                         xyz(Vt) - vw, ri * xyz(Wt), xyz(Wt) - Om, us, ur, ut);
+    HistD hn;
+    hn.us[0] = us.x; hn.us[1] = us.y; hn.us[2] = us.z;
+    hn.ur[0] = ur.x; hn.ur[1] = ur.y; hn.ur[2] = ur.z;
+    hn.ut = ut;
+    hn.stamp = stamp_new;
+    hn.pad = 0;
+    *hp = hn;
+    c6[0] = o.f.x; c6[1] = o.f.y; c6[2] = o.f.z;
+    c6[3] = o.ti.x; c6[4] = o.ti.y; c6[5] = o.ti.z;
+    return true;
+  }
+
+  // Element contacts (unless the caller took them already: with_mesh false)
+  // and integration of particle slot t.
   static __device__ __forceinline__ void finish(const Params& p, const StateBufs& sb,
                                                 uint32_t ph, const ListBuf& lb,
                                                 const MeshDev& mesh, int t, uint32_t ntc_u,
-                                                const D4& Pt, const D4& Vt, const D4& Wt,
-                                                Acc& sums, uint32_t stamp_now,
+                                                bool with_mesh, const D4& Pt, const D4& Vt,
+                                                const D4& Wt, Acc& sums, uint32_t stamp_now,
                                                 uint32_t stamp_new, double* forces,
                                                 uint32_t& nmesh, bool& disp, bool& bad) {
-    const int n = p.n;
-    const int ntc = (int)ntc_u;
+    const int ntc = with_mesh ? (int)ntc_u : 0;
     const D4* Q = static_cast<const D4*>(buf_of(sb.Q, ph));
     if (Pt.w == 0.0) {  // inactive (awaiting spawning): carried over unchanged
       static_cast<D4*>(buf_of(sb.P, ph ^ 1u))[t] = Pt;
@@ -144,54 +200,12 @@ struct Fp64Policy {
     }
     V3<double>& F = sums.F;
     V3<double>& T = sums.T;
-    // particle-triangle contacts
-    if (ntc > 0) {
-      LawConst<double> cpw{p.Es_pw, p.Gs_pw, p.beta, p.mu_s, p.mu_r, p.mu_t, p.dt};
-      if (p.n_mat > 0) {  // the particle's material
-        const D4 a = p.mat_d[(int)Wt.w];
-        cpw.mu_s = a.x;
-        cpw.mu_r = a.y;
-        cpw.mu_t = a.z;
-      }
-      HistD* hpm = static_cast<HistD*>(lb.hpm);
-      const V3<double> x = xyz(Pt);
-      const V3<double> Om = mk(p.mesh_omega[0], p.mesh_omega[1], p.mesh_omega[2]);
-      const V3<double> ctr = mk(p.mesh_center[0], p.mesh_center[1], p.mesh_center[2]);
-      for (int m = 0; m < ntc; ++m) {
-        const uint32_t kt = lb.tric[(size_t)m * n + t];
-        const D4 A = mesh.cur[4 * kt], B = mesh.cur[4 * kt + 1], C = mesh.cur[4 * kt + 2],
-                 D = mesh.cur[4 * kt + 3];
-        const int nvk = (int)mesh.curf[4 * kt].w;
-        const V3<double> pc = closest_point_element(x, xyz(A), xyz(B), xyz(C), xyz(D), nvk);
-        const V3<double> d = x - pc;
-        const double dist = sqrt(dot(d, d));
-        const double delta = Pt.w + A.w - dist;
-        if (delta < 0.0 || !(dist > 0.0)) continue;
-        const V3<double> nh = (1.0 / dist) * d;
-        const double ri = Pt.w - delta / 2.0;
-        const V3<double> xc = x - ri * nh;
-        const V3<double> vw = cross(Om, xc - ctr);
-        HistD h = hpm[(size_t)m * n + t];
-        V3<double> us = mk(0.0, 0.0, 0.0), ur = us;
-        double ut = 0.0;
-        if (h.stamp == stamp_now) {
-          us = mk(h.us[0], h.us[1], h.us[2]);
-          ur = mk(h.ur[0], h.ur[1], h.ur[2]);
-          ut = h.ut;
-        }
-        const LawOut<double> o = contact_law(cpw, nh, delta, Pt.w, Vt.w, ri, 0.0, 1.0 / ri,
-                                             xyz(Vt) - vw, ri * xyz(Wt), xyz(Wt) - Om, us, ur, ut);
-        HistD hn;
-        hn.us[0] = us.x; hn.us[1] = us.y; hn.us[2] = us.z;
-        hn.ur[0] = ur.x; hn.ur[1] = ur.y; hn.ur[2] = ur.z;
-        hn.ut = ut;
-        hn.stamp = stamp_new;
-        hn.pad = 0;
-        hpm[(size_t)m * n + t] = hn;
-        F = F + o.f;
-        T = T + o.ti;
-        ++nmesh;
-      }
+    // particle-element contacts
+    for (int m = 0; m < ntc; ++m) {
+      double c6[6];
+      if (!mesh_contact(p, mesh, lb, t, m, Pt, Vt, Wt, stamp_now, stamp_new, c6)) continue;
+      sums.add(c6);
+      ++nmesh;
     }
     // semi-implicit Euler + SPIRAL (Sec. 2.3)
     const double R = Pt.w, mass = Vt.w;

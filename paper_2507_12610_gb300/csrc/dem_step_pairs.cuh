@@ -196,7 +196,7 @@ k_gather(Ctl* ctl, Params p, StateBufs sb, Lists L, MeshDev mesh,
       get_out(res + e, !lower, c6);
       acc.add(c6);
     }
-    Pol::finish(p, sb, ph, lb, mesh, t, (meta >> 16) & 0xffu, P[t], V[t], W[t], acc,
+    Pol::finish(p, sb, ph, lb, mesh, t, (meta >> 16) & 0xffu, true, P[t], V[t], W[t], acc,
                 stamp_now, stamp_new, forces, nmesh, disp, bad);
   }
   count_and_flag(ctl, 0u, nmesh, disp, bad);

@@ -14,7 +14,9 @@
 //      the parked contributions of its own particle in queue order;
 //      A and B alternate in rounds whenever the queue is full, which keeps
 //      the order and bounds the shared memory;
-//   C. each lane finishes its particle: triangle contacts, integration.
+//   M. the lanes evaluate the particle-element contacts of the warp's
+//      particles 32 candidates at a time and add them in order, as in B;
+//   C. each lane integrates its particle.
 // The sum of every particle is therefore taken in exactly the order of the
 // per-particle loop (ascending partner caller index, then triangle index),
 // whatever the launch shape.  Policies supply the precision-specific parts.
@@ -167,11 +169,49 @@ k_step_warp(Ctl* ctl, Params p, StateBufs sb, Lists L, MeshDev mesh, double* for
     }
   } while (e0 < E);
 
-  // C: triangle contacts and integration of the lane's own particle
+  // M: particle-element contacts of the warp's particles, 32 candidates at a
+  // time (all lanes busy), then ordered sums as in B: every lane adds the
+  // touching contacts of its own particle in candidate (element index) order
   uint32_t nmesh = 0;
+  {
+    const uint32_t nt_l = valid ? (meta >> 16) & 0xffu : 0u;
+    const uint32_t mincl = warp_incl_scan(nt_l);
+    __syncwarp();
+    S.seg[lane + 1] = mincl;
+    if (lane == 0) S.seg[0] = 0;
+    const uint32_t Mt = __shfl_sync(full, mincl, 31);
+    __syncwarp();
+    const uint32_t my_a = S.seg[lane], my_b = S.seg[lane + 1];
+    for (uint32_t c0 = 0; c0 < Mt; c0 += 32) {
+      const uint32_t c = c0 + lane;
+      CT c6[6] = {CT(0), CT(0), CT(0), CT(0), CT(0), CT(0)};
+      bool hit = false;
+      if (c < Mt) {
+        int lo = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1)
+          if (S.seg[lo + step] <= c) lo += step;
+        const int tl = lo;
+        hit = Pol::mesh_contact(p, mesh, lb, w0 + tl, (int)(c - S.seg[tl]), P[w0 + tl],
+                                V[w0 + tl], W[w0 + tl], stamp_now, stamp_new, c6);
+        if (hit) ++nmesh;
+      }
+      const unsigned hm = __ballot_sync(full, hit);
+#pragma unroll
+      for (int k = 0; k < 6; ++k) S.contrib[lane][k] = c6[k];
+      __syncwarp();
+      const uint32_t a = my_a > c0 ? my_a : c0;
+      const uint32_t b = my_b < c0 + 32 ? my_b : c0 + 32;
+      for (uint32_t jj = a; jj < b; ++jj)
+        if (hm >> (jj - c0) & 1u) acc.add(S.contrib[jj - c0]);
+      __syncwarp();
+    }
+  }
+
+  // C: integration of the lane's own particle
   bool disp = false, bad = false;
   if (valid)
-    Pol::finish(p, sb, ph, lb, mesh, t, (meta >> 16) & 0xffu, P[t], V[t],
+    Pol::finish(p, sb, ph, lb, mesh, t, (meta >> 16) & 0xffu, false, P[t], V[t],
                 W[t], acc, stamp_now, stamp_new, forces, nmesh, disp, bad);
 
   count_and_flag(ctl, npair, nmesh, disp, bad);
