@@ -922,7 +922,7 @@ int dem_scene_create(const dem_params* params, const dem_particles* parts, const
     // capacity: for every element, the cells of a cube around its bounding
     // ball grown by the reach (valid for any pose of a rigid mesh)
     const double reach = rmax + skin + 2.0 * p.list_margin;
-    double tcap = 0;
+    double tcap = 0, max_cells = 1;
     for (int k = 0; k < s->nt; ++k) {
       const int4 e = et.el[k];
       const int nvk = ElemTable::count(e);
@@ -940,7 +940,24 @@ int dem_scene_create(const dem_params* params, const dem_particles* parts, const
       }
       const double side = std::ceil(2.0 * (rb + et.rad[k] + reach) / h) + 2.0;
       tcap += std::min((double)ncells, side * side * side);
+      // cells the binning kernel walks for this element: its bounding box
+      // at the reference pose grown by the reach (a turning element's box
+      // changes, which changes only the work per block)
+      double cells = 1;
+      for (int a = 0; a < 3; ++a) {
+        double lo = 1e300, hi = -1e300;
+        for (int j = 0; j < nvk; ++j) {
+          const double x = mesh->vert[3 * ElemTable::vert(e, j) + a];
+          lo = std::min(lo, x);
+          hi = std::max(hi, x);
+        }
+        cells *= std::floor((hi - lo + 2.0 * (et.rad[k] + reach)) / h) + 2.0;
+      }
+      max_cells = std::max(max_cells, cells);
     }
+    // large elements (a floor under a spreading pile) get several blocks each,
+    // about 4096 cells per block
+    p.tri_chunks = (int32_t)std::min(65535.0, std::max(1.0, std::ceil(max_cells / 4096.0)));
     if (tcap > 2.0e9) return fail(DEM_ERR_NOMEM);
     s->bb.tcap = (uint32_t)tcap + 1024;
     s->bb.tcell_tri = M.get<uint32_t>(s->bb.tcap);

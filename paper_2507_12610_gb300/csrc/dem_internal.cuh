@@ -72,6 +72,7 @@ struct Params {
   int32_t n;
   int32_t cap;              // pair-list capacity per particle
   int32_t capm;             // triangle-candidate capacity per particle
+  int32_t tri_chunks;       // blocks per element in the element-cell binning
   int32_t n_tri;
   int32_t record_forces;
   int32_t mixed;

@@ -137,7 +137,8 @@ k_permute(const Ctl* ctl, Params p, BinBuf bb, StateBufs sb, Lists L) {
 // Cells within reach of triangle k: its bounding box grown by the reach
 // R_k + R_max + skin (+ margin), then a conservative per-cell test: the cell
 // centre within reach + half the cell diagonal of the triangle.  pass 0
-// counts, pass 1 fills.  One block per triangle.
+// counts, pass 1 fills.  blockIdx.x is the element; its cells are shared by
+// the gridDim.y blocks of that element.
 __global__ void k_tri_cells(const Ctl* ctl, Params p, MeshDev mesh, BinBuf bb, int pass) {
   if (!rebuilding(ctl)) return;
   const int k = blockIdx.x;
@@ -161,7 +162,8 @@ __global__ void k_tri_cells(const Ctl* ctl, Params p, MeshDev mesh, BinBuf bb, i
   const float lim = reach + halfdiag;
   const V3<float> a = mk(A.x, A.y, A.z), b = mk(B.x, B.y, B.z), c = mk(C.x, C.y, C.z),
                   dd = mk(D.x, D.y, D.z);
-  for (int64_t i = threadIdx.x; i < total; i += blockDim.x) {
+  for (int64_t i = (int64_t)blockIdx.y * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.y * blockDim.x) {
     const int cx = c0.x + (int)(i % nx);
     const int cy = c0.y + (int)((i / nx) % ny);
     const int cz = c0.z + (int)(i / ((int64_t)nx * ny));
@@ -473,11 +475,11 @@ void launch_rebuild(cudaStream_t st, Ctl* ctl, const Params& p, StateBufs sb, Li
     k_permute<D4><<<nb, kThreads, 0, st>>>(ctl, p, bb, sb, L);
   if (mesh.nt > 0) {
     k_clear<<<gcells, kThreads, 0, st>>>(ctl, bb.tcell_count, p.ncells);
-    k_tri_cells<<<(unsigned)mesh.nt, 128, 0, st>>>(ctl, p, mesh, bb, 0);
+    k_tri_cells<<<dim3((unsigned)mesh.nt, (unsigned)p.tri_chunks), 128, 0, st>>>(ctl, p, mesh, bb, 0);
     launch_scan(st, ctl, bb.tcell_count, bb.tcell_start, p.ncells, bb.block_sums);
     k_tri_cells_check<<<1, 1, 0, st>>>(ctl, p, bb);
     k_clear<<<gcells, kThreads, 0, st>>>(ctl, bb.tcell_count, p.ncells);
-    k_tri_cells<<<(unsigned)mesh.nt, 128, 0, st>>>(ctl, p, mesh, bb, 1);
+    k_tri_cells<<<dim3((unsigned)mesh.nt, (unsigned)p.tri_chunks), 128, 0, st>>>(ctl, p, mesh, bb, 1);
     k_tri_cell_sort<<<152 * 8, 32 * kSortWarps, 0, st>>>(ctl, p, bb);
   }
   const unsigned nb128 = blocks_for(p.n, 128);
