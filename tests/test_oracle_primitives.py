@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 from tests import physics as ph
-from tests.test_oracle_pins import E, NU, RHO, head_on, params
+from tests.test_oracle_pins import E, NU, RHO, params
 
 
 def _sample_rect(a, b, d, k, rng):

@@ -2,7 +2,6 @@
 import math
 
 import numpy as np
-import pytest
 
 from paper_2507_12610_gb300 import scenes
 
