@@ -59,6 +59,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <array>
 #include <map>
 #include <utility>
 #include <vector>
@@ -137,6 +138,9 @@ struct Scene {
   std::vector<int32_t> tri;           // [4 nt] vertex indices, -1 pads (1..4 vertices)
   std::vector<double> tri_radius;     // [nt] element radius
   std::map<Key, Hist> hist;
+  // Coulomb ratios (sliding, rolling, twisting) of the contacts of the last
+  // step, same keys as hist; test diagnostics only
+  std::map<Key, std::array<double, 3>> coulomb;
   int64_t step_count = 0;
   int64_t degenerate = 0;  // contacts skipped because d == 0
   oracle_spawn sp{};       // spawning off while sp.attempts == 0
@@ -249,7 +253,15 @@ V3 rotate(V3 r, V3 k, double th) {
 // Friction spring of mode m in {s, r} (Sec. 2.3): project the stored spring
 // onto the current tangent plane and restore its length, evaluate
 // f = -k u - c v, then apply the Coulomb limit mu |f_n| and update u.
-V3 friction_vec(V3& u, V3 n, V3 vm, double k, double c, double mu, double fn_mag, double dt) {
+// Coulomb ratio |f| / (mu |f_n|) of a trial force (a diagnostic for tests:
+// near 1 the static/kinetic decision is within rounding of either branch).
+double coulomb_ratio(double flen, double lim) {
+  if (lim > 0.0) return flen / lim;
+  return flen > 0.0 ? INFINITY : 0.0;
+}
+
+V3 friction_vec(V3& u, V3 n, V3 vm, double k, double c, double mu, double fn_mag, double dt,
+                double* ratio = nullptr) {
   // projection back onto the tangent plane, length preserved (zero if degenerate)
   double ulen = norm(u);
   V3 ut = u - dot(u, n) * n;
@@ -260,6 +272,7 @@ V3 friction_vec(V3& u, V3 n, V3 vm, double k, double c, double mu, double fn_mag
     u = v3(0, 0, 0);
   V3 f = -k * u - c * vm;
   double flen = norm(f);
+  if (ratio) *ratio = coulomb_ratio(flen, mu * fn_mag);
   if (flen <= mu * fn_mag) {
     u = u + dt * vm;  // static regime
   } else {
@@ -269,8 +282,10 @@ V3 friction_vec(V3& u, V3 n, V3 vm, double k, double c, double mu, double fn_mag
   return f;
 }
 
-double friction_scalar(double& u, double vm, double k, double c, double mu, double fn_mag, double dt) {
+double friction_scalar(double& u, double vm, double k, double c, double mu, double fn_mag, double dt,
+                       double* ratio = nullptr) {
   double f = -k * u - c * vm;
+  if (ratio) *ratio = coulomb_ratio(std::fabs(f), mu * fn_mag);
   if (std::fabs(f) <= mu * fn_mag) {
     u = u + dt * vm;
   } else {
@@ -330,7 +345,7 @@ struct Friction {
 ContactOut contact_law(const oracle_params& p, const Friction& mu, V3 nhat, double delta,
                        double Ri, double mi, V3 vi, V3 wi,
                        bool wall, double Rj, double mj, V3 vj, V3 wj, V3 vwall,
-                       Hist& h, bool literal_sign) {
+                       Hist& h, bool literal_sign, double* coul = nullptr) {
   const Coeffs k = contact_coeffs(p, wall, Ri, mi, Rj, mj, delta);
   const double Rs = k.Rs;
   const double kn = k.kn, ks = k.ks, cn = k.cn, cs = k.cs;
@@ -357,9 +372,9 @@ ContactOut contact_law(const oracle_params& p, const Friction& mu, V3 nhat, doub
   const V3 fn = -kn * un - cn * vn;
   const double fn_mag = norm(fn);
   // friction modes, each independently static or kinetic
-  const V3 fs = friction_vec(h.us, nhat, vs, ks, cs, mu.mu_s, fn_mag, p.dt);
-  const V3 fr = friction_vec(h.ur, nhat, vr, kr, cr, mu.mu_r, fn_mag, p.dt);
-  const double ft = friction_scalar(h.ut, vt, kt, ct, mu.mu_t, fn_mag, p.dt);
+  const V3 fs = friction_vec(h.us, nhat, vs, ks, cs, mu.mu_s, fn_mag, p.dt, coul);
+  const V3 fr = friction_vec(h.ur, nhat, vr, kr, cr, mu.mu_r, fn_mag, p.dt, coul ? coul + 1 : nullptr);
+  const double ft = friction_scalar(h.ut, vt, kt, ct, mu.mu_t, fn_mag, p.dt, coul ? coul + 2 : nullptr);
   // torques
   const V3 tau_s = ri * cross(fs, nhat);
   const V3 tau_r = Rs * cross(nhat, fr);
@@ -494,6 +509,7 @@ void step_once(Scene& S) {
   std::fill(S.F.begin(), S.F.end(), 0.0);
   std::fill(S.T.begin(), S.T.end(), 0.0);
   std::map<Key, Hist> next;
+  std::map<Key, std::array<double, 3>> next_coul;
 
   // particle-particle contacts, each unordered pair evaluated once (i < j)
   for (int64_t i = 0; i < n; ++i) {
@@ -511,10 +527,12 @@ void step_once(Scene& S) {
       auto it = S.hist.find(Key(i, j));
       if (it != S.hist.end()) h = it->second;
       const double Rj = S.R[j];
+      std::array<double, 3> cr{};
       ContactOut o = contact_law(p, friction_of_pair(S, i, j), nhat, delta, Ri, mi, vi, wi,
                                  false, Rj, mass_of(p, Rj),
                                  load3(S.v.data(), j), load3(S.w.data(), j), v3(0, 0, 0), h,
-                                 p.literal_sign != 0);
+                                 p.literal_sign != 0, cr.data());
+      next_coul[Key(i, j)] = cr;
       store3(S.F.data(), i, load3(S.F.data(), i) + o.f);
       store3(S.F.data(), j, load3(S.F.data(), j) - o.f);
       store3(S.T.data(), i, load3(S.T.data(), i) + o.tau_i);
@@ -546,16 +564,19 @@ void step_once(Scene& S) {
         const double ri = Ri - delta / 2.0;
         const V3 xc = xi - ri * nhat;  // contact point
         const V3 vwall = cross(Om, xc - c);
+        std::array<double, 3> cr{};
         ContactOut o = contact_law(p, friction_of(S, i), nhat, delta, Ri, mi, vi, wi, true,
                                    INFINITY, INFINITY,
-                                   v3(0, 0, 0), Om, vwall, h, false);
+                                   v3(0, 0, 0), Om, vwall, h, false, cr.data());
         store3(S.F.data(), i, load3(S.F.data(), i) + o.f);
         store3(S.T.data(), i, load3(S.T.data(), i) + o.tau_i);
         next[key] = h;
+        next_coul[key] = cr;
       }
     }
   }
   S.hist.swap(next);
+  S.coulomb.swap(next_coul);
 
   // semi-implicit Euler with the SPIRAL quaternion update (Sec. 2.3)
   for (int64_t i = 0; i < n; ++i) {
@@ -692,6 +713,29 @@ void oracle_set_contacts(void* s, int64_t m, const int64_t* keys, const double* 
 }
 
 void oracle_set_step_count(void* s, int64_t c) { static_cast<Scene*>(s)->step_count = c; }
+
+// Replace the particle state (caller order, n rows of the scene): the tests
+// start a step of the oracle from a state taken elsewhere.
+void oracle_set_state(void* s, const double* x, const double* v, const double* w,
+                      const double* q) {
+  Scene* S = static_cast<Scene*>(s);
+  std::memcpy(S->x.data(), x, sizeof(double) * 3 * S->n);
+  std::memcpy(S->v.data(), v, sizeof(double) * 3 * S->n);
+  std::memcpy(S->w.data(), w, sizeof(double) * 3 * S->n);
+  std::memcpy(S->q.data(), q, sizeof(double) * 4 * S->n);
+}
+
+// Coulomb ratios |f_m| / (mu_m |f_n|) of the trial forces of the last step,
+// m = sliding, rolling, twisting, out[3k..3k+2] for the k-th contact in the
+// order of oracle_read_contacts (a contact near 1 sits at its Coulomb bound).
+void oracle_read_coulomb(void* s, double* out) {
+  Scene* S = static_cast<Scene*>(s);
+  int64_t k = 0;
+  for (const auto& kv : S->coulomb) {
+    std::memcpy(out + 3 * k, kv.second.data(), 3 * sizeof(double));
+    ++k;
+  }
+}
 
 // Closest point on a triangle, exposed for tests.
 void oracle_closest_on_triangle(const double* p, const double* a, const double* b,

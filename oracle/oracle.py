@@ -97,6 +97,8 @@ def _load():
     lib.oracle_read_contacts.argtypes = [_P, ctypes.POINTER(_I64), dp]
     lib.oracle_set_contacts.argtypes = [_P, _I64, ctypes.POINTER(_I64), dp]
     lib.oracle_set_step_count.argtypes = [_P, _I64]
+    lib.oracle_set_state.argtypes = [_P, dp, dp, dp, dp]
+    lib.oracle_read_coulomb.argtypes = [_P, dp]
     lib.oracle_closest_on_triangle.argtypes = [dp, dp, dp, dp, dp]
     lib.oracle_closest_on_element.argtypes = [dp, dp, ctypes.c_int32, dp]
     lib.oracle_beta.restype = _D
@@ -263,6 +265,21 @@ class OracleScene:
         hist = _f64(hist, (-1, 7))
         self._lib.oracle_set_contacts(self._h, keys.shape[0],
                                       keys.ctypes.data_as(ctypes.POINTER(_I64)), _dptr(hist))
+
+    def set_state(self, x, v, w, q) -> None:
+        """Replace x, v, w, q (caller order, all rows) with the given arrays."""
+        n = self.n
+        x, v, w, q = _f64(x, (n, 3)), _f64(v, (n, 3)), _f64(w, (n, 3)), _f64(q, (n, 4))
+        self._lib.oracle_set_state(self._h, _dptr(x), _dptr(v), _dptr(w), _dptr(q))
+
+    def coulomb(self) -> np.ndarray:
+        """Coulomb ratios |f_m| / (mu_m |f_n|) (sliding, rolling, twisting) of
+        the trial forces of the last step, rows in the order of contacts()."""
+        m = int(self._lib.oracle_num_contacts(self._h))
+        out = np.empty((m, 3))
+        if m:
+            self._lib.oracle_read_coulomb(self._h, _dptr(out))
+        return out
 
     @property
     def degenerate(self) -> int:
