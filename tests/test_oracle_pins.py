@@ -667,3 +667,58 @@ def test_hertzian_damping_gives_e_n_exactly_in_the_continuum():
         for v0 in (0.05, 0.5):
             assert ratio(e_n, v0) == pytest.approx(e_n, abs=1e-8)
     assert abs(ratio(0.5, 0.5, fac=4.0) - 0.5) > 0.02
+
+
+# --- tangential restitution of the shear dashpot (Sec. 2.2, Eq. cs) ---------
+
+@pytest.mark.parametrize("e_n", [0.2, 0.5, 0.9])
+def test_tangential_restitution_of_the_shear_dashpot(oracle_mod, e_n):
+    # Sec. 2.2 fixes c_s = sqrt(m* k_s / 6) beta (Eq. cs) and states that it was
+    # tuned numerically so that a central collision with the sliding spring
+    # held at zero gives e_s = e_n.  With u_s = 0 the tangential contact
+    # velocity obeys m_t dv_s/dt = -c_s v_s, where 1/m_t = 1/m_i + 1/m_j +
+    # r_i^2/I_i + r_j^2/I_j = 7/(2 m*) for equal solid spheres turning freely
+    # (r ~ R); the normal overlap obeys m* delta'' = -k_n delta - c_n delta',
+    # and the Hertzian damping of Eq. cn gives ln e_n = -integral c_n dt / (2 m*)
+    # over the contact (both damping coefficients scale as delta^(1/4)).  Hence
+    # ln e_s = -integral c_s dt / m_t = kappa ln e_n with
+    # kappa = (c_s / c_n) (2 m* / m_t) = 7 sqrt((1 - nu) / (10 (2 - nu))),
+    # the printed same-material ratio c_s / c_n.  So e_s = e_n^kappa: the
+    # claim e_s = e_n would need c_s / c_n = 1/7; with the printed factor
+    # kappa = 1.42 at nu = 0.3 (e_s = 0.37 for e_n = 0.5).  The oracle follows
+    # the printed equation; this pins its tangential dashpot and the
+    # kinematics of its contact velocity to that closed form.
+    # a small tangential speed keeps the collision central (the contact normal
+    # turns by a negligible angle); the tangential equation is linear, so e_s
+    # does not depend on that speed
+    # (a slow impact keeps delta << R, so r_i = R_i - delta/2 stays close to R)
+    R, v0, vt0 = 1e-3, 0.01, 1e-6
+    m = ph.sphere_mass(RHO, R)
+    _, tc = ph.hertz_impact(m / 2, R / 2, E / (2 * (1 - NU ** 2)), v0)
+    dt = tc / 2000
+    big = 1e6  # Coulomb bounds never reached: every step is static
+    p = params(e_n=e_n, mu_s=big, mu_r=big, mu_t=big, dt=dt)
+    x = np.array([[-R - 0.25 * v0 * dt, 0, 0], [R + 0.25 * v0 * dt, 0, 0]])
+    v = np.array([[0.5 * v0, 0.5 * vt0, 0], [-0.5 * v0, -0.5 * vt0, 0]])
+    sc = oracle_mod.OracleScene(p, [R, R], x, v)
+    started = False
+    for _ in range(20000):
+        sc.step(1)
+        k, h = sc.contacts()
+        if len(k):
+            started = True
+            sc.set_contacts(k, np.zeros_like(h))  # the sliding spring held at zero
+        elif started:
+            break
+    assert started
+    s = sc.state()
+    d = s["x"][0] - s["x"][1]
+    nh = d / np.linalg.norm(d)
+    vc = s["v"][0] - s["v"][1] + np.cross(nh, R * s["w"][0] + R * s["w"][1])
+    vs = vc - np.dot(vc, nh) * nh
+    e_s = float(np.linalg.norm(vs) / vt0)
+    e_norm = float(np.dot(s["v"][0] - s["v"][1], nh) / v0)  # separating along nh
+    kappa = 7.0 * math.sqrt((1 - NU) / (10 * (2 - NU)))
+    assert abs(e_norm - e_n) < 5e-3 * e_n + 1e-3
+    assert abs(math.log(e_s) / math.log(e_n) - kappa) < 1e-2 * kappa, (e_s, e_n ** kappa, e_n)
+    assert kappa > 1.4 and e_s < e_n  # the printed factor does not give e_s = e_n
