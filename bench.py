@@ -19,6 +19,7 @@ on a bounded sample of the same workload (a 2,000-sphere drum).
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import os
 import subprocess
@@ -44,10 +45,14 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=1_000_000)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--settle", type=int, default=1500)
+    ap.add_argument("--settle", type=int, default=6000,
+                    help="steps before timing: the lattice collapses into the dense "
+                         "flowing bed (contacts per particle level off by ~6000 steps)")
     ap.add_argument("--frame", type=int, default=100, help="steps per state read-back (e2e)")
     ap.add_argument("--fp64-steps", type=int, default=0, help="0: steps // 20")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cpu-design", action="store_true",
+                    help="skip the OpenMP paper-design CPU program")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-ensemble section")
     ap.add_argument("--batch-scenes", type=int, default=512)
@@ -64,60 +69,135 @@ def dist_env():
 
 
 class ClockSampler:
-    """nvidia-smi clock / throttle sampling while the timed region runs."""
+    """SM clock and throttle reasons sampled while the timed region runs.
 
+    Polls NVML (libnvidia-ml, through ctypes) every millisecond from a thread,
+    so even a region of a few milliseconds gets samples; falls back to
+    `nvidia-smi -lms 100` when NVML cannot be loaded.  Reason bits are those
+    of nvmlClocksEventReasons (nvml.h).
+    """
+
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu_index: int):
         self.idx = gpu_index
+        self.samples = []  # (sm_mhz, max_mhz, reason bits)
+        self.source = None
+        self._stop = threading.Event()
         self.proc = None
-        self.lines = []
+        self.t = None
+
+    def _nvml_handle(self):
+        import ctypes
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        h = ctypes.c_void_p()
+        uuid = None
+        try:
+            import torch
+            u = getattr(torch.cuda.get_device_properties(self.idx), "uuid", None)
+            if u is not None:
+                uuid = str(u)
+                if not uuid.startswith("GPU-"):
+                    uuid = "GPU-" + uuid
+        except Exception:
+            uuid = None
+        rc = 1
+        if uuid:
+            rc = lib.nvmlDeviceGetHandleByUUID(uuid.encode(), ctypes.byref(h))
+        if rc != 0:
+            vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+            ids = [c.strip() for c in vis.split(",") if c.strip()]
+            phys = int(ids[self.idx]) if self.idx < len(ids) and ids[self.idx].isdigit() \
+                else self.idx
+            rc = lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(phys), ctypes.byref(h))
+        if rc != 0:
+            raise OSError("no NVML handle")
+        get_reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        return lib, h, get_reasons
+
+    def _poll_nvml(self, lib, h, get_reasons):
+        import ctypes
+        clk, mx, rs = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+        while True:
+            ok = (lib.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(clk)) == 0
+                  and lib.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0
+                  and get_reasons(h, ctypes.byref(rs)) == 0)
+            if ok:
+                self.samples.append((float(clk.value), float(mx.value), int(rs.value)))
+            if self._stop.wait(0.001):
+                break
+
+    def _read_smi(self):
+        for line in self.proc.stdout:
+            f = [c.strip() for c in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                bits = 0
+                for b, val in zip((0x8, 0x40, 0x20, 0x4), f[5:9]):
+                    if val.lower() in ("active", "0x1", "1"):
+                        bits |= b
+                self.samples.append((float(f[1]), float(f[2]), bits))
+            except ValueError:
+                continue
 
     def __enter__(self):
         try:
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
-                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.t = threading.Thread(target=self._read, daemon=True)
+            lib, h, gr = self._nvml_handle()
+            self.source = "nvml"
+            self.t = threading.Thread(target=self._poll_nvml, args=(lib, h, gr), daemon=True)
             self.t.start()
-        except (OSError, FileNotFoundError):
-            self.proc = None
+        except (OSError, AttributeError):
+            try:
+                self.proc = subprocess.Popen(
+                    ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                     "--format=csv,noheader,nounits", "-lms", "100"],
+                    stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                self.source = "nvidia-smi"
+                self.t = threading.Thread(target=self._read_smi, daemon=True)
+                self.t.start()
+            except (OSError, FileNotFoundError):
+                self.proc = None
+        # the timed region starts once the first sample is in
+        t0 = time.time()
+        while self.t is not None and not self.samples and time.time() - t0 < 5.0:
+            time.sleep(0.001)
+        self.n_before = len(self.samples)
         return self
 
-    def _read(self):
-        for line in self.proc.stdout:
-            self.lines.append(line.strip())
-
     def __exit__(self, *a):
+        self._stop.set()
         if self.proc is not None:
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
+        if self.t is not None:
+            self.t.join(timeout=5)
 
     def summary(self):
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            f = [c.strip() for c in ln.split(",")]
-            if len(f) < 9:
-                continue
-            try:
-                sm.append(float(f[1]))
-                mx.append(float(f[2]))
-            except ValueError:
-                continue
-            for name, val in zip(names, f[5:9]):
-                if val.lower() in ("active", "0x1", "1"):
+        # samples taken after the region started (the one before it as well
+        # if the region was too short for its own)
+        smp = self.samples[self.n_before:] or self.samples[-1:]
+        if not smp:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0,
+                    "source": self.source}
+        reasons = set()
+        for _, _, bits in smp:
+            for b, name in self.REASONS.items():
+                if bits & b:
                     reasons.add(name)
-        if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
-                "reasons": sorted(reasons), "samples": len(sm)}
+        return {"sm_mhz": float(np.median([c for c, _, _ in smp])),
+                "sm_max_mhz": float(max(m for _, m, _ in smp)), "reasons": sorted(reasons),
+                "samples": len(smp), "source": self.source}
 
 
 def max_over_ranks(x: float, world: int, device: str = "cpu") -> float:
@@ -165,6 +245,33 @@ def algorithmic_bytes(n: int, st: dict, mixed: bool) -> int:
     pair = 2 * (28 if mixed else 56) + 8
     return int(n * state + 4 * st["list_entries"] + 4 * st["mesh_candidates"]
                + pair * (st["pair_contacts"] + st["mesh_contacts"]))
+
+
+# FP64 operations of one step, counted from the law as the library writes it
+# (each +, -, *, /, sqrt one operation; static springs with history; the
+# divisions and roots expand to several FP64-pipe instructions on the GPU):
+# per touching particle pair the geometry (13), the unit normal (4), R*, m*,
+# r_i, r_j (9), the rolling radius (3), relative velocities (15), stiffness
+# and damping (11), contact velocities (41), normal force and its square (15),
+# two vector springs (98), the twisting spring (8) and the torques (46) -- 263
+# -- plus 6 additions into each of the two particles' sums: 275; per mesh
+# contact about 330 (closest point, wall velocity, the law, one sum); per
+# particle the integration, 190 (accelerations with drag 27, positions and
+# velocities 12, two SPIRAL factors from their series 84 and the two
+# quaternion products 56, spin 6, inertia and drag rates 5).
+FP64_FLOPS_PER_PAIR = 275
+FP64_FLOPS_PER_MESH_CONTACT = 330
+FP64_FLOPS_PER_PARTICLE = 190
+# GB300 double precision: 1.25 TFLOP/s nominal (2 FP64 FMAs per SM and clock
+# at 2.07 GHz on 152 SMs)
+NOMINAL_FP64_TFLOPS = 1.25
+
+
+def fp64_algorithmic_flops(n: int, st: dict) -> int:
+    """FP64 operations one DEM_FP64 step must do (counts of the last step)."""
+    return int(FP64_FLOPS_PER_PAIR * st["pair_contacts"]
+               + FP64_FLOPS_PER_MESH_CONTACT * st["mesh_contacts"]
+               + FP64_FLOPS_PER_PARTICLE * n)
 
 
 def kernel_sources_sha1() -> str:
@@ -312,11 +419,36 @@ def bench_ours(a):
         e1.synchronize()
         rc64 = sd.synchronize()
         t64 = rank_max(e0.elapsed_time(e1) / 1e3)
-        ph64 = sd.step_timed(max(5, k64 // 4))
+        k_ph = max(5, k64 // 4)
+        ph64 = sd.step_timed(k_ph)
+        st64 = sd.stats()
+        kms = ph64[2] / k_ph
+        fma_rate = dem.probe_fp64_fma(stream=ctypes.c_void_p(strm.cuda_stream))
+        peak_tf = 2.0 * fma_rate / 1e12
+        flops = fp64_algorithmic_flops(n, st64)
+        ach_tf = flops / (kms * 1e-3) / 1e12
+        bytes64 = algorithmic_bytes(n, st64, False)
+        ach_gb = bytes64 / (kms * 1e-3) / 1e9
         out["fp64"] = {"value": aggregate_rate(n, k64, t64, world), "ms_per_step": t64 / k64 * 1e3,
-                       "steps": k64, "status": rc64,
-                       "step_kernel_ms": ph64[2] / max(5, k64 // 4),
-                       "bound": "alu (FP64 pipe)"}
+                       "steps": k64, "status": rc64, "step_kernel_ms": kms,
+                       "roofline": {"bound": "alu", "achieved": ach_tf, "peak": peak_tf,
+                                    "unit": "TFLOP/s", "frac": ach_tf / peak_tf,
+                                    "traffic": measured_traffic(n, False),
+                                    "kernel": "k_pairs+k_gather<Fp64Policy>",
+                                    "peak_source": "measured: dem_probe_fp64_fma (FP64 FMA "
+                                                   "rate x 2 flops) on this GPU",
+                                    "nominal_peak_tflops": NOMINAL_FP64_TFLOPS,
+                                    "algorithmic_flops_per_step": flops,
+                                    "flop_counting": "FP64 operations of the law as written "
+                                                     "(+, -, *, /, sqrt each 1): 275 per "
+                                                     "touching pair (law and both sums), 330 "
+                                                     "per mesh contact, 190 per particle "
+                                                     "(integration)",
+                                    "hbm": {"achieved": ach_gb, "peak": peaks["hbm_gbs"],
+                                            "unit": "GB/s", "frac": ach_gb / peaks["hbm_gbs"],
+                                            "algorithmic_bytes_per_launch": bytes64}},
+                       "pair_contacts": st64["pair_contacts"],
+                       "mesh_contacts": st64["mesh_contacts"]}
         sd.close()
 
     # end to end through the C ABI with host buffers: create from host arrays
@@ -367,6 +499,10 @@ def bench_ours(a):
 
     if rank == 0 and not a.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(target_s=15.0)
+        if not a.no_cpu_design:
+            from paper_2507_12610_gb300 import scenes
+            out["cpu_paper_design"] = cpu_paper_design(
+                s_set, scenes.box_scene(n=1000, seed=1, speed=0.3))
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -454,54 +590,117 @@ def bench_surrogate(dem, strm, n=100_000):
                     "its trajectory error is measured by paper_2507_12610_gb300.surrogate"}
 
 
-def oracle_sample():
+def oracle_sample(seed: int = 5):
     """A bounded sample of the drum workload the O(N^2) oracle can step."""
     from paper_2507_12610_gb300 import scenes
-    return scenes.drum_scene(n=2000, seed=5, n_theta=32, n_rings=4, nn_dist=2.15e-3, speed=0.02)
+    return scenes.drum_scene(n=2000, seed=seed, n_theta=32, n_rings=4, nn_dist=2.15e-3,
+                             speed=0.02)
 
 
-def cpu_baseline(target_s: float = 15.0, steps: int | None = None):
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_on_cores(steps: int | None = None, warmup: int = 3, target_s: float = 15.0,
+                    cores: int | None = None):
+    """The oracle as it stands on every host core: one independent 2,000-sphere
+    drum sample per core (seeds 5, 6, ...), each stepped by its own thread
+    (the oracle's ctypes calls release the GIL, so the threads run in
+    parallel).  Returns (particle-steps/s over all cores, cores, steps, s)."""
     from oracle import oracle
-    s = oracle_sample()
-    oc = oracle.OracleScene(s["params"], s["R"], s["x"], s["v"], s["w"], s["q"], s["verts"],
-                            s["tris"], s["tri_radius"])
-    t0 = time.perf_counter()
-    oc.step(3)
-    per = (time.perf_counter() - t0) / 3
+    oracle.build()
+    cores = cores or host_cores()
+    ocs = []
+    for k in range(cores):
+        s = oracle_sample(seed=5 + k)
+        ocs.append(oracle.OracleScene(s["params"], s["R"], s["x"], s["v"], s["w"], s["q"],
+                                      s["verts"], s["tris"], s["tri_radius"]))
+    n = len(ocs[0].state()["x"])
+
+    def run_all(k):
+        th = [threading.Thread(target=oc.step, args=(k,)) for oc in ocs]
+        t0 = time.perf_counter()
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        return time.perf_counter() - t0
+
+    per = run_all(warmup) / max(warmup, 1)
     k = steps or max(5, int(target_s / max(per, 1e-6)))
-    t0 = time.perf_counter()
-    oc.step(k)
-    el = time.perf_counter() - t0
-    n = len(s["R"])
-    return {"value": n * k / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{n}-sphere drum (same radii, material, 30 rpm; {len(s['tris'])} "
-                      f"triangles), FP64 O(N^2) oracle, {k} steps, {el:.1f} s, 1 thread"}
+    el = run_all(k)
+    return cores * n * k / el, cores, k, el, n
+
+
+def cpu_baseline(target_s: float = 15.0):
+    value, cores, k, el, n = oracle_on_cores(target_s=target_s)
+    return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{cores} independent {n}-sphere drum samples (same radii, material, "
+                      f"30 rpm; 320 triangles), one per host core, FP64 O(N^2) oracle, "
+                      f"{k} steps each, {el:.1f} s"}
+
+
+# The paper's own timings (Sec. 5): one step of N = 1,000 settled spheres in a
+# cube took about 0.64 ms on a 3.6 GHz 8-core Intel Xeon Gold 6244; serial
+# Cundall numbers (particle updates per second) from 3.5e6 down to 3.2e5 for
+# N up to 10 million.
+PAPER_TIMINGS = {
+    "hardware": "Intel Xeon Gold 6244, 3.6 GHz, 8 cores (2019), GCC 11.2 -O3",
+    "n1000_ms_per_step": 0.64,
+    "n1000_particle_steps_per_s": 1000 / 0.64e-3,
+    "serial_particle_steps_per_s_range": [3.5e6, 3.2e5],
+    "source": "Sec. 5 (computational performance), settled spheres in a cube",
+}
+
+
+def cpu_paper_design(drum: dict, box: dict, target_s: float = 10.0):
+    """The OpenMP cell-list program in the paper's design (baseline/dem_cpu.cpp)
+    on all host cores: the 1,000-sphere box pour and the settled 1M-sphere
+    drum (a few steps each, bounded by target_s)."""
+    from baseline import dem_cpu
+    from paper_2507_12610_gb300 import scenes
+    out = {"kind": "OpenMP cell-list program in the paper's design (linked cells of edge "
+                   "2 R_max rebuilt every step, one evaluation per pair, FP64)",
+           "cores": dem_cpu.threads(), "cpu": dem_cpu.cpu_model(), "unit": UNIT,
+           "paper": PAPER_TIMINGS}
+    for name, s, warm in (("box_1000", box, 20), ("drum_1M", drum, 1)):
+        V, El, rad = scenes.all_elements(s)
+        cs = dem_cpu.CpuScene(s["params"], s["R"], s["x"], s["v"], s["w"], s["q"], V, El, rad)
+        t0 = time.perf_counter()
+        cs.step(warm)
+        per = (time.perf_counter() - t0) / warm
+        k = max(2, min(2000, int(target_s / 2 / max(per, 1e-6))))
+        t0 = time.perf_counter()
+        cs.step(k)
+        el = time.perf_counter() - t0
+        n = len(s["R"])
+        out[name] = {"value": n * k / el, "ms_per_step": el / k * 1e3, "steps": k,
+                     "n_particles": n}
+        del cs
+    return out
 
 
 def bench_reference(a):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    from oracle import oracle
-    oracle.build()
-    s = oracle_sample()
-    oc = oracle.OracleScene(s["params"], s["R"], s["x"], s["v"], s["w"], s["q"], s["verts"],
-                            s["tris"], s["tri_radius"])
-    n = len(s["R"])
-    oc.step(a.warmup)
-    t0 = time.perf_counter()
-    oc.step(a.steps)
-    el = time.perf_counter() - t0
-    value = n * a.steps / el
+    # each step of this arm is `cores` oracle steps (one per host core) on
+    # independent 2,000-sphere samples of the drum workload
+    value, cores, k, el, n = oracle_on_cores(steps=a.steps, warmup=a.warmup)
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
            "steps": a.steps, "warmup": a.warmup, "ms_per_step": el / a.steps * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic",
            "config": {"workload": "rotating drum sample for the CPU oracle: 2,000 spheres "
-                                  "R~U[0.8,1.2] mm, 320-triangle cylinder at 30 rpm",
-                      "n_particles": n},
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                            "sample": f"{n}-sphere drum, {a.steps} steps, 1 thread"},
+                                  "R~U[0.8,1.2] mm, 320-triangle cylinder at 30 rpm, one "
+                                  "independent sample per host core",
+                      "n_particles": n * cores},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": f"{cores} x {n}-sphere drum, {a.steps} steps, "
+                                      f"one thread per core"},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)

@@ -44,7 +44,9 @@ extern "C" {
 #define DEM_ERR_INVALID 1   /* argument violates the requirements of Table 2 or the layout */
 #define DEM_ERR_CAPACITY 2  /* a neighbour or mesh-contact list overflowed its capacity */
 #define DEM_ERR_NONFINITE 3 /* a particle state became NaN or infinite */
-#define DEM_ERR_TIMEOUT 4   /* a bounded device wait gave up */
+#define DEM_ERR_TIMEOUT 4   /* reserved for a bounded device wait that gives up; no
+                               kernel of this library waits on another (kernel
+                               boundaries order the phases), so none returns it */
 #define DEM_ERR_CUDA 5      /* a CUDA runtime call failed */
 #define DEM_ERR_NOMEM 6     /* device memory allocation failed */
 
@@ -54,6 +56,10 @@ extern "C" {
                        velocities, spins and orientations integrated as
                        compensated double-float pairs (two FP32 words, ~48-bit
                        significand); forces summed with compensated FP32 */
+#define DEM_MIXED64 2 /* contact forces, torques and friction springs in FP32
+                         (the overlap and the pair offset formed in FP64, then
+                         rounded); positions, velocities, spins and
+                         orientations stored and accumulated in FP64 */
 
 /* Material, kinetic and numerical parameters.  Physical parameters follow
  * Table 2 of the paper and must satisfy its "Requirements" column:
@@ -77,7 +83,7 @@ typedef struct dem_params {
   double skin;           /* Verlet skin (m); <= 0 selects 0.25 R_max */
   double domain_lo[3];   /* binning box (m); if any lo >= hi the box is the */
   double domain_hi[3];   /*   bounding box of particles and mesh, padded     */
-  int32_t precision;     /* DEM_FP64 or DEM_MIXED */
+  int32_t precision;     /* DEM_FP64, DEM_MIXED or DEM_MIXED64 */
   int32_t max_neighbors; /* list capacity per particle; <= 0 selects 64 */
   int32_t max_mesh_contacts; /* mesh-element candidate capacity per particle; <= 0: 16 */
   int32_t record_forces; /* nonzero: keep per-particle contact sums for dem_read_forces */
@@ -181,8 +187,11 @@ int dem_scene_create(const dem_params* params, const dem_particles* particles,
 
 /* Enqueue `nsteps` time steps on the scene's stream and return without
  * waiting.  Each step: mesh pose, rebuild check, (cell binning, Verlet list and
- * history remap when needed), contact forces, gather and integration.
- * Errors found on the device are reported by dem_synchronize(). */
+ * history remap when needed: Sec. 3.3 and the Verlet lists suggested in Sec.
+ * 7), contact forces (Sec. 2.2), gather and semi-implicit Euler + SPIRAL
+ * integration (Sec. 2.3).  Errors found on the device (DEM_ERR_CAPACITY,
+ * DEM_ERR_NONFINITE) are sticky and reported by dem_synchronize(); returns
+ * DEM_ERR_INVALID (nsteps < 0) or DEM_ERR_CUDA at once. */
 int dem_step(dem_scene* s, int64_t nsteps);
 
 /* Like dem_step, but launches each step phase by phase (no CUDA graph) with
@@ -197,7 +206,8 @@ int dem_step_timed(dem_scene* s, int64_t nsteps, double* phase_ms);
 /* Wait for the scene's stream; return the sticky device status. */
 int dem_synchronize(dem_scene* s);
 
-/* Copy the current state to host arrays in caller order, n_cap rows (see
+/* Copy the current state (the particle variables x, v, omega, q of Sec. 2.1
+ * and Table 3) to host arrays in caller order, n_cap rows (see
  * dem_params.n_max); any pointer may be NULL.  Rows of inactive particles
  * hold zeros and the identity orientation.  The conversion to absolute
  * doubles and the reordering run on the device (into a staging buffer the
@@ -213,7 +223,8 @@ int dem_read_radii(dem_scene* s, double* R);
  * caller order.  Requires params.record_forces.  Synchronizes. */
 int dem_read_forces(dem_scene* s, double* F, double* T);
 
-/* Active contacts of the last step with their friction history.  keys[2k] = i,
+/* Active contacts of the last step with their friction history (the contact
+ * list c of Table 3, Sec. 3.2: partner j, springs u_s, u_r, u_t).  keys[2k] = i,
  * keys[2k+1] = j in caller indices: a particle pair has i < j; a mesh
  * contact has j = -1 - element index (see dem_mesh).  hist[7k..7k+6] = u_s (3), u_r (3), u_t.
  * Rows are sorted by (i, j).  If `capacity` is too small only the count is
@@ -223,28 +234,41 @@ int dem_read_contacts(dem_scene* s, int64_t capacity, int64_t* keys, double* his
 
 int dem_get_stats(dem_scene* s, dem_stats* out);
 
-/* Serialise the complete scene (parameters, state, contact history, step
- * count) into `buf`.  With buf == NULL, writes the required size to *len. */
+/* Serialise the complete scene (parameters, state, contact history of Sec.
+ * 3.2 / Table 3, step count) into `buf`, a host buffer of *len bytes; with
+ * buf == NULL, writes the required size to *len.  Synchronizes.  Errors: the
+ * sticky device status, except DEM_ERR_CAPACITY: an overflowing list is found
+ * while the lists are rebuilt, before the step does any work, so the state
+ * and history of the last completed step are intact and still saved (regrow:
+ * load the blob into a scene created with larger capacities and step on).
+ * DEM_ERR_CAPACITY is also returned (with *len set) if *len is too small. */
 int dem_save(dem_scene* s, void* buf, size_t* len);
 
-/* Restore a scene saved by dem_save (same particle count and mesh). */
+/* Restore a scene saved by dem_save into `s`, which must have the same
+ * particle count, mesh and precision (capacities may differ); the next step
+ * rebuilds the lists.  Clears the sticky status.  Synchronizes.  Errors:
+ * DEM_ERR_INVALID (not a blob of this scene's shape), DEM_ERR_CAPACITY (a
+ * particle has more saved contacts than this scene's capacity), DEM_ERR_CUDA. */
 int dem_load(dem_scene* s, const void* buf, size_t len);
 
 void dem_scene_destroy(dem_scene* s);
 
 /* Contact force and torque sums of a particle state that has no friction
  * history yet (the first step of a run), for callers that cannot allocate
- * device memory: code running inside a CUDA stream capture or a real-time
- * loop, where an allocation would break the capture or stall, and hosts whose
- * device memory is owned by another allocator (a framework's caching pool)
- * that must stay the only one.  The paper has no counterpart of this entry
- * point; it is a packaging of the library's FP64 first-step arithmetic.
+ * device memory: a real-time loop, where an allocation can stall for an
+ * unbounded time, and hosts whose device memory is owned by another allocator
+ * (a framework's caching pool) that must stay the only one.  The paper has no
+ * counterpart of this entry point; it is a packaging of the library's FP64
+ * first-step arithmetic.
  *
  * Inputs and outputs are DEVICE arrays of the caller: R[n], x[n][3], v[n][3],
  * w[n][3] in, F[n][3] and T[n][3] out (contact sums only: no gravity, no drag).
  * Only particle pairs are considered (no mesh).  The cell grid covers
- * params->domain_lo .. domain_hi with cells of edge 2 r_max (r_max >= every R);
- * particles outside are clamped to the boundary cells.  Material parameters
+ * params->domain_lo .. domain_hi with cells of edge 2 r_max.  Every particle
+ * must lie inside that box and have 0 < R <= r_max, else the call returns
+ * DEM_ERR_INVALID; a cell holding more than 64 particles returns
+ * DEM_ERR_CAPACITY (both found on the device, after which the remaining
+ * kernels return at once and F, T are left unspecified).  Material parameters
  * come from params (precision and list fields are ignored).
  *
  * Memory: nothing is allocated.  Scratch is one fixed device array inside the
@@ -264,6 +288,17 @@ int dem_contact_forces_noalloc(const dem_params* params, int64_t n, double r_max
                                const double* w, double* F, double* T, void* stream);
 
 const char* dem_status_string(int status);
+
+/* Measurement utility (not part of the timestep): the FP64 fused multiply-add
+ * throughput of the current device, in FMAs per second, measured with a
+ * kernel of 8 blocks of 256 threads per SM, each thread running 8 independent
+ * FMA chains of `iters` steps (best of two timed launches after one warm-up,
+ * CUDA events on `stream`, a cudaStream_t or NULL).  It is the denominator of
+ * the roofline of the DEM_FP64 step, which the FP64 pipe bounds (GB300 runs
+ * double precision at about 1/64 of its FP32 rate).  Allocates and frees a
+ * small device buffer and synchronizes the stream.  Errors: DEM_ERR_INVALID
+ * (iters <= 0 or fma_per_s NULL), DEM_ERR_NOMEM, DEM_ERR_CUDA. */
+int dem_probe_fp64_fma(int64_t iters, void* stream, double* fma_per_s);
 
 #ifdef __cplusplus
 }

@@ -19,7 +19,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdem.so")
 
 SOURCES = ["dem_api.cu", "dem_rebuild.cu", "dem_scan.cu", "dem_step.cu", "dem_step_fp64.cu",
-           "dem_noalloc.cu", "dem_spawn.cu", "dem_export.cu", "mpnn.cu"]
+           "dem_noalloc.cu", "dem_spawn.cu", "dem_export.cu", "mpnn.cu", "dem_probe.cu"]
 # the FP64 step is the precision reference: no multiply-add contraction
 # the mixed step uses approximate FP32 division and square root (about 1 ulp);
 # its compensated sums use neither

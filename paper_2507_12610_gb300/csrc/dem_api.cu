@@ -46,6 +46,16 @@ bool fp64_two_sided() {
   return env && env[0] == '1';
 }
 
+#ifndef DEM_MIXED_PAIRS
+#define DEM_MIXED_PAIRS 0
+#endif
+// Whether the step evaluates each pair once (pair kernel + gather kernel)
+// rather than from both sides in one kernel.
+bool one_eval_per_pair(const Params& p) {
+  if (p.mixed64) return false;
+  return p.mixed ? DEM_MIXED_PAIRS != 0 : !fp64_two_sided();
+}
+
 bool finite_all(const double* a, int64_t n) {
   for (int64_t i = 0; i < n; ++i)
     if (!std::isfinite(a[i])) return false;
@@ -181,7 +191,8 @@ int validate(const dem_params* pr, const dem_particles* pa, const dem_mesh* me) 
   if (!(pr->e_n >= 0 && pr->e_n <= 1)) return DEM_ERR_INVALID;
   if (pr->mu_s < 0 || pr->mu_r < 0 || pr->mu_t < 0 || pr->eta < 0) return DEM_ERR_INVALID;
   if (!(pr->dt > 0)) return DEM_ERR_INVALID;
-  if (pr->precision != DEM_FP64 && pr->precision != DEM_MIXED) return DEM_ERR_INVALID;
+  if (pr->precision != DEM_FP64 && pr->precision != DEM_MIXED && pr->precision != DEM_MIXED64)
+    return DEM_ERR_INVALID;
   if (pr->max_neighbors > 64 || pr->max_mesh_contacts > 255) return DEM_ERR_INVALID;
   // spawning (Sec. 3.1)
   const bool spawn = pr->spawn_attempts != 0;
@@ -416,7 +427,7 @@ int fetch_contacts(dem_scene* s, const Ctl& c, std::vector<ContactRow>& rows) {
   }
   const uint32_t want = (uint32_t)c.step;  // stamp written by the last completed step
   auto decode = [&](const unsigned char* rec, ContactRow& r) {
-    if (s->p.mixed) {
+    if (s->p.hist32) {
       HistM h;
       std::memcpy(&h, rec, sizeof h);
       for (int q = 0; q < 3; ++q) r.h[q] = h.us[q], r.h[3 + q] = h.ur[q];
@@ -493,7 +504,7 @@ int install_contacts(dem_scene* s, const std::vector<ContactRow>& rows, uint32_t
   std::vector<uint32_t> nbr(E);
   std::vector<unsigned char> hpp(E * s->hist_bytes), hpm(maxnt * n * s->hist_bytes);
   auto encode = [&](const ContactRow& r, unsigned char* rec) {
-    if (s->p.mixed) {
+    if (s->p.hist32) {
       HistM h;
       for (int q = 0; q < 3; ++q) h.us[q] = (float)r.h[q], h.ur[q] = (float)r.h[3 + q];
       h.ut = (float)r.h[6];
@@ -721,6 +732,11 @@ int dem_scene_create(const dem_params* params, const dem_particles* parts, const
   p.f_Es_pw = (float)p.Es_pw;
   p.f_Gs_pw = (float)p.Gs_pw;
   p.f_beta = (float)p.beta;
+  // c_s / c_n = sqrt(G* / (5 E*)) for either kind of contact (Eqs. cn, cs)
+  p.cs_cn_pp = std::sqrt(p.Gs_pp / (5.0 * p.Es_pp));
+  p.cs_cn_pw = std::sqrt(p.Gs_pw / (5.0 * p.Es_pw));
+  p.f_cs_cn_pp = (float)p.cs_cn_pp;
+  p.f_cs_cn_pw = (float)p.cs_cn_pw;
   p.f_mu_s = (float)p.mu_s;
   p.f_mu_r = (float)p.mu_r;
   p.f_mu_t = (float)p.mu_t;
@@ -734,12 +750,14 @@ int dem_scene_create(const dem_params* params, const dem_particles* parts, const
                            p.mesh_omega[2] * p.mesh_omega[2]);
   s->static_mesh = !(p.omega_norm > 0.0);
   p.mixed = params->precision == DEM_MIXED ? 1 : 0;
+  p.mixed64 = params->precision == DEM_MIXED64 ? 1 : 0;
+  p.hist32 = p.mixed || p.mixed64;
   p.record_forces = params->record_forces ? 1 : 0;
   p.n = (int32_t)n;
   p.n_tri = s->nt;
   p.cap = params->max_neighbors > 0 ? params->max_neighbors : 64;
   p.capm = params->max_mesh_contacts > 0 ? params->max_mesh_contacts : 16;
-  s->hist_bytes = p.mixed ? sizeof(HistM) : sizeof(HistD);
+  s->hist_bytes = p.hist32 ? sizeof(HistM) : sizeof(HistD);
   p.step_warps = params->step_warps == 8 ? 8 : 4;
   p.sp_attempts = spawning ? params->spawn_attempts : 0;
   p.sp_every = params->spawn_every > 0 ? params->spawn_every : 1;
@@ -890,7 +908,7 @@ int dem_scene_create(const dem_params* params, const dem_particles* parts, const
     lb.offs = M.get<uint32_t>(n + 1);
     lb.nbr = M.get<uint32_t>((size_t)p.cap * n);
     lb.hpp = M.get<unsigned char>((size_t)p.cap * n * s->hist_bytes);
-    if (!p.mixed && !fp64_two_sided()) {
+    if (one_eval_per_pair(p)) {
       lb.mir = M.get<uint32_t>((size_t)p.cap * n);
       lb.back = M.get<uint8_t>((size_t)p.cap * n);
     }
@@ -911,7 +929,7 @@ int dem_scene_create(const dem_params* params, const dem_particles* parts, const
   s->bb.tmp_offs = M.get<uint32_t>(n + 1);
   if (p.record_forces) s->forces = M.get<double>(6 * (size_t)n);
   s->export_buf = M.get<double>(13 * (size_t)n);
-  if (!p.mixed && !fp64_two_sided()) {  // DEM_FP64: one evaluation per pair
+  if (one_eval_per_pair(p)) {  // one evaluation per pair
     p.pair_res = M.get<unsigned char>((size_t)p.cap * n * pair_result_bytes());
     p.pair_touch = M.get<unsigned long long>((size_t)n);
   }
@@ -1228,7 +1246,11 @@ int dem_save(dem_scene* s, void* buf, size_t* len) {
   Ctl c;
   int rc = read_ctl(s, &c);
   if (rc != DEM_OK) return rc;
-  if (c.status) return (int)c.status;
+  // a capacity overflow is found while the lists are rebuilt, before the step
+  // does any work: the state and contact history of the last completed step
+  // are intact, so they can still be saved (and restored into a scene with
+  // larger capacities)
+  if (c.status && c.status != DEM_ERR_CAPACITY) return (int)c.status;
   HostState h;
   rc = fetch_state(s, c, h);
   if (rc != DEM_OK) return rc;

@@ -49,6 +49,7 @@ struct Params {
   double beta;           // damping factor of e_n (Sec. 2.2)
   double Es_pp, Gs_pp;   // effective moduli particle-particle (same material)
   double Es_pw, Gs_pw;   // particle-wall limits
+  double cs_cn_pp, cs_cn_pw;  // c_s / c_n of a pair and of a wall contact
   double mesh_omega[3], mesh_center[3];
   double omega_norm;     // |mesh_omega|
   double mesh_rmax;      // largest vertex distance from the rotation axis
@@ -66,6 +67,7 @@ struct Params {
   float mesh_prefilter;     // float margin before the FP64 triangle geometry (mixed)
   // FP32 copies of the constants for DEM_MIXED (no FP64 conversion in the hot loop)
   float f_Es_pp, f_Gs_pp, f_Es_pw, f_Gs_pw, f_beta, f_mu_s, f_mu_r, f_mu_t, f_dt;
+  float f_cs_cn_pp, f_cs_cn_pw;
   float f_g[3], f_omega[3];
   float f_drag;             // 9 eta / (2 rho): Stokes rate c = f_drag / R^2
   float center_hi[3], center_lo[3];  // mesh_center - origin as hi/lo floats
@@ -75,7 +77,9 @@ struct Params {
   int32_t tri_chunks;       // blocks per element in the element-cell binning
   int32_t n_tri;
   int32_t record_forces;
-  int32_t mixed;
+  int32_t mixed;            // DEM_MIXED: compensated FP32 state records (F8)
+  int32_t mixed64;          // DEM_MIXED64: FP64 state records, FP32 contact law
+  int32_t hist32;           // friction springs in FP32 (DEM_MIXED, DEM_MIXED64)
   // spawning (n above is the capacity; see Ctl::n_active)
   double sp_lo[3], sp_hi[3];
   double sp_rmin, sp_rmax;

@@ -18,6 +18,8 @@ struct LawConst {
   T beta;        // damping factor of e_n
   T mu_s, mu_r, mu_t;
   T dt;
+  T cs_cn;       // c_s / c_n = sqrt(G* / (5 E*)) (Eqs. cn, cs with k_s / k_n = 6 G* / E*);
+                 // used in single precision only
 };
 
 template <typename T>
@@ -33,7 +35,11 @@ __device__ __forceinline__ float vabs(float a) { return fabsf(a); }
 // Friction spring of mode s or r (Eqs. um .. um_kinetic): project onto the
 // tangent plane keeping the length (zero if degenerate), evaluate
 // f = -k u - c v, keep it if |f| <= mu |f_n| (static: u += dt v), otherwise
-// clip it to mu |f_n| and set u = -(f + c v) / k (kinetic).
+// clip it to mu |f_n| and set u = -(f + c v) / k (kinetic).  A contact that
+// slid in the last step meets its bound again within rounding when nothing
+// changed, so the test compares the lengths as the printed inequality does
+// (the double-precision path then decides exactly as a plain double-precision
+// program of the printed equations).
 template <typename T>
 __device__ __forceinline__ V3<T> spring_vec(V3<T>& u, V3<T> n, V3<T> vm, T k, T c, T mu, T fn,
                                             T dt) {
@@ -73,24 +79,26 @@ __device__ __forceinline__ T spring_scalar(T& u, T vm, T k, T c, T mu, T fn, T d
 
 // One contact.  dv = v_i - v_j (pair) or v_i - v_wall at the contact point
 // (wall); rw = r_i w_i + r_j w_j (pair) or r_i w_i (wall), the rotational part
-// of the contact velocity; om = w_i - w_j (wall: w_i - Omega).  rs_inv is
-// 1/r_i + 1/r_j (wall: 1/r_i); rj is unused for walls.  The callers form the
-// differences so each precision can do it without cancellation.
+// of the contact velocity; om = w_i - w_j (wall: w_i - Omega).  reff is the
+// rolling radius (1/r_i + 1/r_j)^-1 (wall: r_i); rj is unused for walls.  The
+// callers form the differences so each precision can do it without
+// cancellation.
 template <typename T>
 __device__ __forceinline__ LawOut<T> contact_law(const LawConst<T>& c, V3<T> n, T delta, T Rs,
-                                                 T ms, T ri, T rj, T rs_inv, V3<T> dv, V3<T> rw,
+                                                 T ms, T ri, T rj, T reff, V3<T> dv, V3<T> rw,
                                                  V3<T> om, V3<T>& us, V3<T>& ur, T& ut) {
   // stiffness and damping (Eqs. ks, cn, cs; k_r = k_n, k_t = k_s, c_r = c_n, c_t = c_s)
   const T a = vsqrt(Rs * delta);
   const T kn = T(4) / T(3) * c.Es * a;
   const T ks = T(8) * c.Gs * a;
   const T cn = vsqrt(T(5) * ms * kn) * c.beta;
-  const T cs = vsqrt(ms * ks / T(6)) * c.beta;
+  // double precision keeps the printed form (and its rounding);
+  // single precision scales c_n by the constant ratio (one root fewer)
+  const T cs = sizeof(T) == 8 ? vsqrt(ms * ks / T(6)) * c.beta : cn * c.cs_cn;
   // relative velocity at the contact point
   const V3<T> v = dv + cross(n, rw);
   const V3<T> vn = dot(v, n) * n;
   const V3<T> vs = v - vn;
-  const T reff = T(1) / rs_inv;
   const V3<T> vr = reff * cross(om, n);
   const T vt = Rs * dot(om, n);
   // normal force f_n = -k_n u_n - c_n v_n with u_n = -delta n

@@ -84,20 +84,24 @@ __device__ __forceinline__ ff ff_add(ff a, ff b) {
 }
 __device__ __forceinline__ ff ff_neg(ff a) { return ff{-a.hi, -a.lo}; }
 
-// Compensated accumulator of a 3-vector (Kahan-Babuska style, order fixed).
+// Kahan's compensated summation (Kahan 1965), the compensation kept as a
+// correction term: sum = h + l.  The rounding error of each addition is
+// carried into the next one; the order of the additions is fixed.
+__device__ __forceinline__ void kahan(float& h, float& l, float b) {
+  const float y = b + l;
+  const float t = h + y;
+  l = y - (t - h);
+  h = t;
+}
+
+// Compensated accumulator of a 3-vector (order fixed by the caller).
 struct Acc3 {
   float hx, hy, hz, lx, ly, lz;
   __device__ __forceinline__ void zero() { hx = hy = hz = lx = ly = lz = 0.f; }
   __device__ __forceinline__ void add(V3<float> v) {
-    ff a = two_sum(hx, v.x);
-    hx = a.hi;
-    lx += a.lo;
-    ff b = two_sum(hy, v.y);
-    hy = b.hi;
-    ly += b.lo;
-    ff c = two_sum(hz, v.z);
-    hz = c.hi;
-    lz += c.lo;
+    kahan(hx, lx, v.x);
+    kahan(hy, ly, v.y);
+    kahan(hz, lz, v.z);
   }
 };
 

@@ -27,6 +27,7 @@ constexpr int64_t kNoAllocMaxCells = 262144;      // 2^18
 constexpr int kTile = 4096;                       // scan tile (elements per block)
 constexpr int64_t kMaxTiles = kNoAllocMaxCells / kTile + 1;
 constexpr int kMaxTouching = 64;                  // touching partners per particle
+constexpr uint32_t kMaxPerCell = 64;              // particles per grid cell
 
 // scratch layout (u32 words)
 constexpr int64_t kOffKey = 0;
@@ -42,7 +43,7 @@ constexpr int64_t kScratchWords = kOffStatus + 1;
 __device__ __align__(256) uint32_t g_noalloc_scratch[kScratchWords];
 
 struct Grid {
-  double lo[3];
+  double lo[3], hi[3];
   double inv_h;
   int32_t nc[3];
   int32_t ncells;
@@ -67,17 +68,58 @@ __global__ void na_clear(uint32_t* s, int64_t ncells) {
   if (blockIdx.x == 0 && threadIdx.x == 0) s[kOffStatus] = 0u;
 }
 
-__global__ void na_bin(uint32_t* s, Grid g, const double* x, int64_t n) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const uint32_t c = cell_of(g, x[3 * i], x[3 * i + 1], x[3 * i + 2]);
-  s[kOffKey + i] = c;
-  s[kOffLocal + i] = atomicAdd(&s[kOffCount + c], 1u);
+__device__ __forceinline__ void na_fail(uint32_t* s, uint32_t code) {
+  atomicCAS(&s[kOffStatus], 0u, code);
 }
 
-// exclusive scan of the cell counts: tile totals, scan of the totals, tiles
-__global__ void na_scan_tiles(uint32_t* s, int64_t ncells) {
-  __shared__ uint32_t part[256];
+// Cell of each particle.  A radius outside (0, r_max], a non-finite or
+// out-of-domain position (DEM_ERR_INVALID) or a cell holding more than
+// kMaxPerCell particles (DEM_ERR_CAPACITY) sets the status word; the later
+// kernels then return at once, so a wrong domain or radius bound cannot make
+// the call walk one crowded cell for a long time.
+__global__ void na_bin(uint32_t* s, Grid g, const double* R, const double* x, int64_t n,
+                       double r_max) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double px = x[3 * i], py = x[3 * i + 1], pz = x[3 * i + 2], r = R[i];
+  const double p3[3] = {px, py, pz};
+  bool ok = r > 0.0 && r <= r_max;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) ok = ok && p3[a] >= g.lo[a] && p3[a] <= g.hi[a];  // false for NaN
+  uint32_t c = 0;
+  if (ok) {
+    c = cell_of(g, px, py, pz);
+    const uint32_t k = atomicAdd(&s[kOffCount + c], 1u);
+    if (k >= kMaxPerCell) na_fail(s, (uint32_t)DEM_ERR_CAPACITY);
+    s[kOffLocal + i] = k;
+  } else {
+    na_fail(s, (uint32_t)DEM_ERR_INVALID);
+    s[kOffLocal + i] = 0u;
+  }
+  s[kOffKey + i] = c;
+}
+
+// Exclusive scan of the cell counts: tile totals (one block per tile of
+// kTile cells), an exclusive scan of the totals (one warp), then every tile
+// scanned in shared memory (256 threads, kTile / 256 consecutive cells each).
+// The result is the same whatever the launch shape (integer sums).
+constexpr int kScanThreads = 256;
+constexpr int kPerThread = kTile / kScanThreads;
+
+__device__ __forceinline__ uint32_t warp_excl_scan(uint32_t v, uint32_t& total) {
+  const int lane = threadIdx.x & 31;
+  uint32_t incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  total = __shfl_sync(0xffffffffu, incl, 31);
+  return incl - v;
+}
+
+__global__ void __launch_bounds__(kScanThreads) na_scan_tiles(uint32_t* s, int64_t ncells) {
+  __shared__ uint32_t part[kScanThreads];
   const int64_t base = (int64_t)blockIdx.x * kTile;
   uint32_t sum = 0;
   for (int k = threadIdx.x; k < kTile; k += blockDim.x) {
@@ -93,38 +135,57 @@ __global__ void na_scan_tiles(uint32_t* s, int64_t ncells) {
   if (threadIdx.x == 0) s[kOffTiles + blockIdx.x] = part[0];
 }
 
+// one warp: exclusive scan of the tile totals, 32 at a time with a carry
 __global__ void na_scan_top(uint32_t* s, int64_t ntiles) {
-  if (threadIdx.x != 0) return;
-  uint32_t acc = 0;
-  for (int64_t t = 0; t < ntiles; ++t) {
-    const uint32_t v = s[kOffTiles + t];
-    s[kOffTiles + t] = acc;
-    acc += v;
+  uint32_t carry = 0;
+  for (int64_t t0 = 0; t0 < ntiles; t0 += 32) {
+    const int64_t t = t0 + threadIdx.x;
+    const uint32_t v = t < ntiles ? s[kOffTiles + t] : 0u;
+    uint32_t total;
+    const uint32_t ex = warp_excl_scan(v, total);
+    if (t < ntiles) s[kOffTiles + t] = carry + ex;
+    carry += total;
   }
-  s[kOffTiles + ntiles] = acc;
+  if (threadIdx.x == 0) s[kOffTiles + ntiles] = carry;
 }
 
-__global__ void na_scan_down(uint32_t* s, int64_t ncells, int64_t ntiles) {
-  if (threadIdx.x != 0) return;  // one thread per tile walks it in order
-  const int64_t base = (int64_t)blockIdx.x * kTile;
-  uint32_t acc = s[kOffTiles + blockIdx.x];
-  for (int k = 0; k < kTile; ++k) {
-    const int64_t i = base + k;
-    if (i >= ncells) break;
-    s[kOffStart + i] = acc;
-    acc += s[kOffCount + i];
+__global__ void __launch_bounds__(kScanThreads) na_scan_down(uint32_t* s, int64_t ncells,
+                                                             int64_t ntiles) {
+  __shared__ uint32_t wsum[kScanThreads / 32];
+  const int64_t base = (int64_t)blockIdx.x * kTile + (int64_t)threadIdx.x * kPerThread;
+  uint32_t v[kPerThread];
+  uint32_t mine = 0;
+#pragma unroll
+  for (int k = 0; k < kPerThread; ++k) {
+    v[k] = base + k < ncells ? s[kOffCount + base + k] : 0u;
+    mine += v[k];
   }
-  if (blockIdx.x == ntiles - 1) s[kOffStart + ncells] = s[kOffTiles + ntiles];
+  // exclusive prefix of the threads' sums within the block
+  uint32_t wtotal;
+  const uint32_t ex = warp_excl_scan(mine, wtotal);
+  const int warp = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) wsum[warp] = wtotal;
+  __syncthreads();
+  uint32_t before = 0;
+  for (int k = 0; k < warp; ++k) before += wsum[k];
+  uint32_t acc = s[kOffTiles + blockIdx.x] + before + ex;
+#pragma unroll
+  for (int k = 0; k < kPerThread; ++k) {
+    if (base + k < ncells) s[kOffStart + base + k] = acc;
+    acc += v[k];
+  }
+  if (blockIdx.x == ntiles - 1 && threadIdx.x == 0) s[kOffStart + ncells] = s[kOffTiles + ntiles];
 }
 
 __global__ void na_scatter(uint32_t* s, int64_t n) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  if (i >= n || s[kOffStatus] != 0u) return;
   s[kOffOrder + s[kOffStart + s[kOffKey + i]] + s[kOffLocal + i]] = (uint32_t)i;
 }
 
 // within a cell, ascending particle index
 __global__ void na_cell_sort(uint32_t* s, int64_t ncells) {
+  if (s[kOffStatus] != 0u) return;
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncells;
        c += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t a = s[kOffStart + c], b = s[kOffStart + c + 1];
@@ -161,7 +222,7 @@ __device__ __forceinline__ V3<double> ld3(const double* a, int64_t i) {
 // index, each pair evaluated in canonical orientation with zero springs.
 __global__ void __launch_bounds__(128) na_forces(uint32_t* s, Grid g, ForceArgs a) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= a.n) return;
+  if (t >= a.n || s[kOffStatus] != 0u) return;
   const double Rt = a.R[t];
   const uint32_t ct = s[kOffKey + t];
   const int cx = (int)(ct % (uint32_t)g.nc[0]);
@@ -221,7 +282,7 @@ __global__ void __launch_bounds__(128) na_forces(uint32_t* s, Grid g, ForceArgs 
     V3<double> us = mk(0.0, 0.0, 0.0), ur = us;
     double ut = 0.0;
     const LawOut<double> o =
-        contact_law(a.c, nh, delta, Rs, ms, ri, rj, 1.0 / ri + 1.0 / rj,
+        contact_law(a.c, nh, delta, Rs, ms, ri, rj, 1.0 / (1.0 / ri + 1.0 / rj),
                     ld3(a.v, i) - ld3(a.v, j), ri * wi + rj * wj, wi - wj, us, ur, ut);
     if (t_is_i) {
       F = F + o.f;
@@ -294,6 +355,7 @@ extern "C" int dem_contact_forces_noalloc(const dem_params* params, int64_t n, d
     const double c = std::ceil((hi - lo) / h);
     if (!(c >= 1) || c > (double)kNoAllocMaxCells) return DEM_ERR_INVALID;
     g.lo[a] = lo;
+    g.hi[a] = hi;
     g.nc[a] = (int32_t)c;
     ncells *= (int64_t)c;
     if (ncells > kNoAllocMaxCells) return DEM_ERR_INVALID;
@@ -309,15 +371,16 @@ extern "C" int dem_contact_forces_noalloc(const dem_params* params, int64_t n, d
   const double G = E / (2.0 * (1.0 + nu));
   fa.c = LawConst<double>{1.0 / ((1.0 - nu * nu) / E + (1.0 - nu * nu) / E),
                           1.0 / ((2.0 - nu) / G + (2.0 - nu) / G), beta_host(params->e_n),
-                          params->mu_s, params->mu_r, params->mu_t, params->dt};
+                          params->mu_s, params->mu_r, params->mu_t, params->dt, 0.0};
+  fa.c.cs_cn = std::sqrt(fa.c.Gs / (5.0 * fa.c.Es));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int64_t ntiles = (ncells + kTile - 1) / kTile;
   const unsigned nb = (unsigned)((n + 127) / 128);
   na_clear<<<(unsigned)std::min<int64_t>((ncells + 255) / 256, 1024), 256, 0, st>>>(s, ncells);
-  na_bin<<<nb, 128, 0, st>>>(s, g, x, n);
-  na_scan_tiles<<<(unsigned)ntiles, 256, 0, st>>>(s, ncells);
+  na_bin<<<nb, 128, 0, st>>>(s, g, R, x, n, r_max);
+  na_scan_tiles<<<(unsigned)ntiles, kScanThreads, 0, st>>>(s, ncells);
   na_scan_top<<<1, 32, 0, st>>>(s, ntiles);
-  na_scan_down<<<(unsigned)ntiles, 32, 0, st>>>(s, ncells, ntiles);
+  na_scan_down<<<(unsigned)ntiles, kScanThreads, 0, st>>>(s, ncells, ntiles);
   na_scatter<<<nb, 128, 0, st>>>(s, n);
   na_cell_sort<<<(unsigned)std::min<int64_t>((ncells + 255) / 256, 1024), 256, 0, st>>>(s,
                                                                                       ncells);

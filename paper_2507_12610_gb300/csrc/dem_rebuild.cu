@@ -181,7 +181,7 @@ __global__ void k_tri_cells(const Ctl* ctl, Params p, MeshDev mesh, BinBuf bb, i
       hit = dot(d, d) <= lim * lim;
     }
     if (!hit) continue;
-    const uint32_t cell = (uint32_t)((cz * p.nc[1] + cy) * p.nc[0] + cx);
+    const uint32_t cell = cell_index(p, make_int3(cx, cy, cz));
     if (pass == 0) {
       atomicAdd(&bb.tcell_count[cell], 1u);
     } else {
@@ -290,8 +290,8 @@ k_list_build(Ctl* ctl, Params p, BinBuf bb, Lists L, MeshDev mesh) {
     for (int dy = -1; dy <= 1; ++dy) {
       const int cy = c.y + dy;
       if (cy < 0 || cy >= p.nc[1]) continue;
-      const uint32_t row = (uint32_t)((cz * p.nc[1] + cy) * p.nc[0]);
-      const uint32_t a = bb.cell_start[row + x0], b = bb.cell_start[row + x1 + 1];
+      const uint32_t a = bb.cell_start[cell_index(p, make_int3(x0, cy, cz))];
+      const uint32_t b = bb.cell_start[cell_index(p, make_int3(x1, cy, cz)) + 1];
       for (uint32_t u = a; u < b; ++u) {
         if (u == (uint32_t)t) continue;
         const float4 Y = ln.posf[u];
@@ -484,12 +484,12 @@ void launch_rebuild(cudaStream_t st, Ctl* ctl, const Params& p, StateBufs sb, Li
   }
   const unsigned nb128 = blocks_for(p.n, 128);
   const unsigned nb128p = blocks_for((int64_t)p.n + 1, 128);
-  if (p.mixed)
+  if (p.hist32)
     k_list_build<HistM><<<nb128, 128, 0, st>>>(ctl, p, bb, L, mesh);
   else
     k_list_build<HistD><<<nb128, 128, 0, st>>>(ctl, p, bb, L, mesh);
   launch_scan(st, ctl, bb.tmp_cnt, bb.tmp_offs, p.n, bb.block_sums);
-  if (p.mixed)
+  if (p.hist32)
     k_list_compact<HistM><<<nb128p, 128, 0, st>>>(ctl, p, bb, L);
   else
     k_list_compact<HistD><<<nb128p, 128, 0, st>>>(ctl, p, bb, L);

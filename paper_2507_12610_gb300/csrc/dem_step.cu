@@ -18,6 +18,7 @@
 #include "dem_law.cuh"
 #include "dem_math.cuh"
 #include "dem_step_common.cuh"
+#include "dem_step_pairs.cuh"
 #include "dem_step_warp.cuh"
 
 namespace dem {
@@ -141,15 +142,6 @@ __device__ __forceinline__ void acc(float& hi, float& lo, float b) {
 #ifndef DEM_MIXED_MIN_BLOCKS
 #define DEM_MIXED_MIN_BLOCKS 7
 #endif
-
-// sin x: Taylor polynomial to x^7 for |x| < 1/16 (the first omitted term is
-// below 1e-15 relative, far under FP32 rounding), sinf otherwise.  The
-// rotation angles of one step are tiny.
-__device__ __forceinline__ float sin_small(float x) {
-  if (fabsf(x) >= 0.0625f) return sinf(x);
-  const float x2 = x * x;
-  return x * (1.f - x2 * (1.f / 6.f) * (1.f - x2 * (1.f / 20.f) * (1.f - x2 * (1.f / 42.f))));
-}
 
 // Overlap and unit normal (from the element to the particle) of particle
 // record Pt with feature `feat` of mesh element kt, in compensated FP32: the
@@ -325,7 +317,8 @@ struct MixedPolicy {
                                                   uint32_t stamp_new, LawOut<float>& o) {
     Geo g;
     if (!touch(p, Pi, Pj, g)) return false;
-    LawConst<float> cpp{p.f_Es_pp, p.f_Gs_pp, p.f_beta, p.f_mu_s, p.f_mu_r, p.f_mu_t, p.f_dt};
+    LawConst<float> cpp{p.f_Es_pp, p.f_Gs_pp, p.f_beta, p.f_mu_s, p.f_mu_r, p.f_mu_t, p.f_dt,
+                        p.f_cs_cn_pp};
     if (p.n_mat > 0) {  // the mean of the two materials' coefficients
       const float4 a = p.mat_f[__float_as_int(Wi.lo.w)], b = p.mat_f[__float_as_int(Wj.lo.w)];
       cpp.mu_s = (a.x + b.x) * 0.5f;
@@ -343,7 +336,7 @@ struct MixedPolicy {
       ur = mk(h.ur[0], h.ur[1], h.ur[2]);
       ut = h.ut;
     }
-    o = contact_law(cpp, g.n, g.delta, Rs, ms, ri, rj, 1.f / ri + 1.f / rj, diff3(Vi, Vj),
+    o = contact_law(cpp, g.n, g.delta, Rs, ms, ri, rj, ri * rj / (ri + rj), diff3(Vi, Vj),
                     ri * sum3(Wi) + rj * sum3(Wj), diff3(Wi, Wj), us, ur, ut);
     h.us[0] = us.x; h.us[1] = us.y; h.us[2] = us.z;
     h.ur[0] = ur.x; h.ur[1] = ur.y; h.ur[2] = ur.z;
@@ -378,7 +371,8 @@ struct MixedPolicy {
     float delta;
     V3<float> nh;
     if (!mesh_gap(mesh, kt, feat, Pt, Al, Bl, delta, nh)) return false;
-    LawConst<float> cpw{p.f_Es_pw, p.f_Gs_pw, p.f_beta, p.f_mu_s, p.f_mu_r, p.f_mu_t, p.f_dt};
+    LawConst<float> cpw{p.f_Es_pw, p.f_Gs_pw, p.f_beta, p.f_mu_s, p.f_mu_r, p.f_mu_t, p.f_dt,
+                        p.f_cs_cn_pw};
     if (p.n_mat > 0) {  // the particle's material
       const float4 a = p.mat_f[__float_as_int(Wt.lo.w)];
       cpw.mu_s = a.x;
@@ -405,7 +399,7 @@ struct MixedPolicy {
                             (Vt.hi.z - vw.z) + Vt.lo.z);
     const V3<float> om = mk((Wt.hi.x - Om.x) + Wt.lo.x, (Wt.hi.y - Om.y) + Wt.lo.y,
                             (Wt.hi.z - Om.z) + Wt.lo.z);
-    const LawOut<float> o = contact_law(cpw, nh, delta, Rt, Vt.hi.w, ri, 0.f, 1.f / ri, dv,
+    const LawOut<float> o = contact_law(cpw, nh, delta, Rt, Vt.hi.w, ri, 0.f, ri, dv,
                                         ri * sum3(Wt), om, us, ur, ut);
     HistM hn;
     hn.us[0] = us.x; hn.us[1] = us.y; hn.us[2] = us.z;
@@ -471,12 +465,8 @@ struct MixedPolicy {
     // orientation: q <- q (cos phi, sin phi w^) (cos th, sin th al^), applied as
     // q + q (cos - 1, sin axis) so the small increment is formed in FP32 and
     // added to the compensated quaternion
-    const float wn = sqrtf(dot(w0, w0));
-    if (wn > 0.f) {
-      const float phi = 0.5f * dt * wn;
-      const float sh = sin_small(0.5f * phi);
-      const float sp = sin_small(phi);
-      const float r[4] = {-2.f * sh * sh, sp * w0.x / wn, sp * w0.y / wn, sp * w0.z / wn};
+    float r[4];
+    if (rot_factor(0.5f * dt, w0, r)) {
       const float qh[4] = {Qn.hi.x + Qn.lo.x, Qn.hi.y + Qn.lo.y, Qn.hi.z + Qn.lo.z,
                            Qn.hi.w + Qn.lo.w};
       float dq[4];
@@ -486,12 +476,7 @@ struct MixedPolicy {
       acc(Qn.hi.z, Qn.lo.z, dq[2]);
       acc(Qn.hi.w, Qn.lo.w, dq[3]);
     }
-    const float an = sqrtf(dot(al, al));
-    if (an > 0.f) {
-      const float th = (0.5f * dt) * (0.5f * dt) * an;
-      const float sh = sin_small(0.5f * th);
-      const float st = sin_small(th);
-      const float r[4] = {-2.f * sh * sh, st * al.x / an, st * al.y / an, st * al.z / an};
+    if (rot_factor((0.5f * dt) * (0.5f * dt), al, r)) {
       const float qh[4] = {Qn.hi.x + Qn.lo.x, Qn.hi.y + Qn.lo.y, Qn.hi.z + Qn.lo.z,
                            Qn.hi.w + Qn.lo.w};
       float dq[4];
@@ -526,6 +511,239 @@ struct MixedPolicy {
     }
 };
 
+
+// ============================================================================
+// DEM_MIXED64: contact law and springs in FP32, state stored and accumulated
+// in FP64 (the FP32-force / FP64-position mode)
+// ============================================================================
+
+#ifndef DEM_MIXED64_MIN_BLOCKS
+#define DEM_MIXED64_MIN_BLOCKS 6
+#endif
+
+struct Mixed64Policy {
+  static constexpr int kMinBlocks = DEM_MIXED64_MIN_BLOCKS;
+  using Rec = D4;
+  using Hist = HistM;
+  using T = float;
+  using Acc = MixedPolicy::Acc;
+
+  // Conservative pre-test: the offset in FP64, the comparison in FP32 with a
+  // 1e-4 relative margin (symmetric in its arguments).
+  static __device__ __forceinline__ bool near(const D4& a, const D4& b) {
+    const float dx = (float)(a.x - b.x), dy = (float)(a.y - b.y), dz = (float)(a.z - b.z);
+    const float S = (float)(a.w + b.w);
+    return dx * dx + dy * dy + dz * dz <= S * S * 1.0001f;
+  }
+
+  static __device__ __forceinline__ bool pair(const Params& p, bool t_is_i, const D4& Pi,
+                                              const D4& Pj, const D4& Vi, const D4& Vj,
+                                              const D4& Wi, const D4& Wj, HistM& h,
+                                              uint32_t stamp_now, uint32_t stamp_new,
+                                              float c6[6]) {
+    LawOut<float> o;
+    if (!pair_law(p, Pi, Pj, Vi, Vj, Wi, Wj, h, stamp_now, stamp_new, o)) return false;
+    if (t_is_i) {
+      c6[0] = o.f.x; c6[1] = o.f.y; c6[2] = o.f.z;
+      c6[3] = o.ti.x; c6[4] = o.ti.y; c6[5] = o.ti.z;
+    } else {
+      c6[0] = -o.f.x; c6[1] = -o.f.y; c6[2] = -o.f.z;
+      c6[3] = o.tj.x; c6[4] = o.tj.y; c6[5] = o.tj.z;
+    }
+    return true;
+  }
+
+  // The canonical pair (i, j): offset, distance and overlap in FP64 (the
+  // overlap is a small difference of two millimetre lengths), then rounded;
+  // everything after that in FP32.  Velocity and spin differences are formed
+  // in FP64 before rounding, so they keep their relative accuracy.
+  static __device__ __forceinline__ bool pair_law(const Params& p, const D4& Pi, const D4& Pj,
+                                                  const D4& Vi, const D4& Vj, const D4& Wi,
+                                                  const D4& Wj, HistM& h, uint32_t stamp_now,
+                                                  uint32_t stamp_new, LawOut<float>& o) {
+    const double dx = Pi.x - Pj.x, dy = Pi.y - Pj.y, dz = Pi.z - Pj.z;
+    const double d2 = dx * dx + dy * dy + dz * dz;
+    const double S = Pi.w + Pj.w;
+    if (d2 > S * S * (1.0 + 1e-10)) return false;
+    const double dist = sqrt(d2);
+    const double deltad = S - dist;
+    if (!(deltad >= 0.0) || !(dist > 0.0)) return false;
+    const float delta = (float)deltad;
+    const float idist = 1.f / (float)dist;
+    const V3<float> nh = mk((float)dx * idist, (float)dy * idist, (float)dz * idist);
+    LawConst<float> cpp{p.f_Es_pp, p.f_Gs_pp, p.f_beta, p.f_mu_s, p.f_mu_r, p.f_mu_t, p.f_dt,
+                        p.f_cs_cn_pp};
+    if (p.n_mat > 0) {  // the mean of the two materials' coefficients
+      const float4 a = p.mat_f[(int)Wi.w], b = p.mat_f[(int)Wj.w];
+      cpp.mu_s = (a.x + b.x) * 0.5f;
+      cpp.mu_r = (a.y + b.y) * 0.5f;
+      cpp.mu_t = (a.z + b.z) * 0.5f;
+    }
+    const float Ri = (float)Pi.w, Rj = (float)Pj.w;
+    const float mi = (float)Vi.w, mj = (float)Vj.w;
+    const float Rs = Ri * Rj / (Ri + Rj), ms = mi * mj / (mi + mj);
+    const float ri = Ri - 0.5f * delta, rj = Rj - 0.5f * delta;
+    V3<float> us = mk(0.f, 0.f, 0.f), ur = us;
+    float ut = 0.f;
+    if (h.stamp == stamp_now) {
+      us = mk(h.us[0], h.us[1], h.us[2]);
+      ur = mk(h.ur[0], h.ur[1], h.ur[2]);
+      ut = h.ut;
+    }
+    const V3<float> wi = mk((float)Wi.x, (float)Wi.y, (float)Wi.z);
+    const V3<float> wj = mk((float)Wj.x, (float)Wj.y, (float)Wj.z);
+    const V3<float> dv = mk((float)(Vi.x - Vj.x), (float)(Vi.y - Vj.y), (float)(Vi.z - Vj.z));
+    const V3<float> om = mk((float)(Wi.x - Wj.x), (float)(Wi.y - Wj.y), (float)(Wi.z - Wj.z));
+    o = contact_law(cpp, nh, delta, Rs, ms, ri, rj, ri * rj / (ri + rj), dv, ri * wi + rj * wj,
+                    om, us, ur, ut);
+    h.us[0] = us.x; h.us[1] = us.y; h.us[2] = us.z;
+    h.ur[0] = ur.x; h.ur[1] = ur.y; h.ur[2] = ur.z;
+    h.ut = ut;
+    h.stamp = stamp_new;
+    return true;
+  }
+
+  // Particle slot t and its m-th element candidate: the closest point and the
+  // overlap in FP64 (an element is large next to the overlap), the law in FP32.
+  static __device__ __forceinline__ bool mesh_contact(const Params& p, const MeshDev& mesh,
+                                                      const ListBuf& lb, int t, int m,
+                                                      const D4& Pt, const D4& Vt, const D4& Wt,
+                                                      uint32_t stamp_now, uint32_t stamp_new,
+                                                      float c6[6]) {
+    const int n = p.n;
+    const uint32_t kt = lb.tric[(size_t)m * n + t];
+    const V3<double> x = xyz(Pt);
+    const D4 A = mesh.cur[4 * kt], B = mesh.cur[4 * kt + 1], C = mesh.cur[4 * kt + 2],
+             D = mesh.cur[4 * kt + 3];
+    const int nvk = (int)mesh.curf[4 * kt].w;
+    const V3<double> pc = closest_point_element(x, xyz(A), xyz(B), xyz(C), xyz(D), nvk);
+    const V3<double> d = x - pc;
+    const double dist = sqrt(dot(d, d));
+    const double deltad = Pt.w + A.w - dist;
+    if (deltad < 0.0 || !(dist > 0.0)) return false;
+    const float delta = (float)deltad;
+    const float idist = 1.f / (float)dist;
+    const V3<float> nh = mk((float)d.x * idist, (float)d.y * idist, (float)d.z * idist);
+    LawConst<float> cpw{p.f_Es_pw, p.f_Gs_pw, p.f_beta, p.f_mu_s, p.f_mu_r, p.f_mu_t, p.f_dt,
+                        p.f_cs_cn_pw};
+    if (p.n_mat > 0) {  // the particle's material
+      const float4 a = p.mat_f[(int)Wt.w];
+      cpw.mu_s = a.x;
+      cpw.mu_r = a.y;
+      cpw.mu_t = a.z;
+    }
+    const float Rt = (float)Pt.w;
+    const float ri = Rt - 0.5f * delta;
+    const V3<float> Om = mk(p.f_omega[0], p.f_omega[1], p.f_omega[2]);
+    const V3<float> rc = mk((float)(x.x - p.mesh_center[0]), (float)(x.y - p.mesh_center[1]),
+                            (float)(x.z - p.mesh_center[2]));
+    const V3<float> vw = cross(Om, rc - ri * nh);
+    HistM* hp = &static_cast<HistM*>(lb.hpm)[(size_t)m * n + t];
+    const HistM h = *hp;
+    V3<float> us = mk(0.f, 0.f, 0.f), ur = us;
+    float ut = 0.f;
+    if (h.stamp == stamp_now) {
+      us = mk(h.us[0], h.us[1], h.us[2]);
+      ur = mk(h.ur[0], h.ur[1], h.ur[2]);
+      ut = h.ut;
+    }
+    const V3<float> dv = mk((float)(Vt.x - (double)vw.x), (float)(Vt.y - (double)vw.y),
+                            (float)(Vt.z - (double)vw.z));
+    const V3<float> wt = mk((float)Wt.x, (float)Wt.y, (float)Wt.z);
+    const LawOut<float> o = contact_law(cpw, nh, delta, Rt, (float)Vt.w, ri, 0.f, ri, dv,
+                                        ri * wt, wt - Om, us, ur, ut);
+    HistM hn;
+    hn.us[0] = us.x; hn.us[1] = us.y; hn.us[2] = us.z;
+    hn.ur[0] = ur.x; hn.ur[1] = ur.y; hn.ur[2] = ur.z;
+    hn.ut = ut;
+    hn.stamp = stamp_new;
+    *hp = hn;
+    c6[0] = o.f.x; c6[1] = o.f.y; c6[2] = o.f.z;
+    c6[3] = o.ti.x; c6[4] = o.ti.y; c6[5] = o.ti.z;
+    return true;
+  }
+
+  // Element contacts (unless taken already) and integration of slot t: the
+  // accelerations and the SPIRAL increment in FP32 (from FP32 forces), added
+  // to the FP64 velocity, spin and orientation; positions advance in FP64.
+  static __device__ __forceinline__ void finish(const Params& p, const StateBufs& sb,
+                                                uint32_t ph, const ListBuf& lb,
+                                                const MeshDev& mesh, int t, uint32_t ntc_u,
+                                                bool with_mesh, const D4& Pt, const D4& Vt,
+                                                const D4& Wt, Acc& sums, uint32_t stamp_now,
+                                                uint32_t stamp_new, double* forces,
+                                                uint32_t& nmesh, bool& disp, bool& bad) {
+    const int ntc = with_mesh ? (int)ntc_u : 0;
+    const D4* Q = static_cast<const D4*>(buf_of(sb.Q, ph));
+    if (Pt.w == 0.0) {  // inactive (awaiting spawning): carried over unchanged
+      static_cast<D4*>(buf_of(sb.P, ph ^ 1u))[t] = Pt;
+      static_cast<D4*>(buf_of(sb.V, ph ^ 1u))[t] = Vt;
+      static_cast<D4*>(buf_of(sb.W, ph ^ 1u))[t] = Wt;
+      static_cast<D4*>(buf_of(sb.Q, ph ^ 1u))[t] = Q[t];
+      if (p.record_forces)
+        for (int c = 0; c < 6; ++c) forces[6 * (size_t)t + c] = 0.0;
+      return;
+    }
+    for (int m = 0; m < ntc; ++m) {
+      float c6[6];
+      if (!mesh_contact(p, mesh, lb, t, m, Pt, Vt, Wt, stamp_now, stamp_new, c6)) continue;
+      sums.add(c6);
+      ++nmesh;
+    }
+    const Acc3& F = sums.F;
+    const Acc3& T = sums.T;
+    const float R = (float)Pt.w, mass = (float)Vt.w;
+    const float I = 0.4f * mass * R * R;
+    const float ci = p.f_drag / (R * R), gi = 10.f / 3.f * ci;
+    const V3<float> v0 = mk((float)Vt.x, (float)Vt.y, (float)Vt.z);
+    const V3<float> w0 = mk((float)Wt.x, (float)Wt.y, (float)Wt.z);
+    const float im = 1.f / mass, iI = 1.f / I;
+    const V3<float> a = mk((F.hx + F.lx) * im + p.f_g[0] - ci * v0.x,
+                           (F.hy + F.ly) * im + p.f_g[1] - ci * v0.y,
+                           (F.hz + F.lz) * im + p.f_g[2] - ci * v0.z);
+    const V3<float> al = mk((T.hx + T.lx) * iI - gi * w0.x, (T.hy + T.ly) * iI - gi * w0.y,
+                            (T.hz + T.lz) * iI - gi * w0.z);
+    const double dt = p.dt;
+    const V3<double> v = mk(Vt.x + dt * (double)a.x, Vt.y + dt * (double)a.y,
+                            Vt.z + dt * (double)a.z);
+    const V3<double> x = mk(Pt.x + dt * v.x, Pt.y + dt * v.y, Pt.z + dt * v.z);
+    // orientation: q <- q + q (cos phi - 1, sin phi w^), then the same with
+    // the angular acceleration; each increment in FP32, the sum in FP64
+    const D4 q4 = Q[t];
+    double q[4] = {q4.x, q4.y, q4.z, q4.w};
+    float r[4];
+    for (int pass = 0; pass < 2; ++pass) {
+      const bool turn = pass == 0 ? rot_factor(0.5f * p.f_dt, w0, r)
+                                  : rot_factor((0.5f * p.f_dt) * (0.5f * p.f_dt), al, r);
+      if (!turn) continue;
+      const float qf[4] = {(float)q[0], (float)q[1], (float)q[2], (float)q[3]};
+      float dq[4];
+      qmul(qf, r, dq);
+      for (int c = 0; c < 4; ++c) q[c] += (double)dq[c];
+    }
+    const V3<double> w = mk(Wt.x + dt * (double)al.x, Wt.y + dt * (double)al.y,
+                            Wt.z + dt * (double)al.z);
+    static_cast<D4*>(buf_of(sb.P, ph ^ 1u))[t] = make_D4(x.x, x.y, x.z, Pt.w);
+    static_cast<D4*>(buf_of(sb.V, ph ^ 1u))[t] = make_D4(v.x, v.y, v.z, Vt.w);
+    static_cast<D4*>(buf_of(sb.W, ph ^ 1u))[t] = make_D4(w.x, w.y, w.z, Wt.w);
+    static_cast<D4*>(buf_of(sb.Q, ph ^ 1u))[t] = make_D4(q[0], q[1], q[2], q[3]);
+    if (p.record_forces) {
+      double* fo = forces + 6 * (size_t)t;
+      fo[0] = (double)F.hx + (double)F.lx;
+      fo[1] = (double)F.hy + (double)F.ly;
+      fo[2] = (double)F.hz + (double)F.lz;
+      fo[3] = (double)T.hx + (double)T.lx;
+      fo[4] = (double)T.hy + (double)T.ly;
+      fo[5] = (double)T.hz + (double)T.lz;
+    }
+    bad = !isfinite(x.x + x.y + x.z + v.x + v.y + v.z + w.x + w.y + w.z);
+    const float4 pr = lb.posf[t];
+    const float ex = (float)(x.x - p.origin[0]) - pr.x, ey = (float)(x.y - p.origin[1]) - pr.y,
+                ez = (float)(x.z - p.origin[2]) - pr.z;
+    disp = ex * ex + ey * ey + ez * ez >= p.half_skin_trigger * p.half_skin_trigger;
+  }
+};
+
 }  // namespace
 
 void launch_mesh_pose(cudaStream_t st, const Ctl* ctl, const Params& p, MeshDev mesh, int ahead) {
@@ -536,8 +754,13 @@ void launch_mesh_pose(cudaStream_t st, const Ctl* ctl, const Params& p, MeshDev 
 
 void launch_step(cudaStream_t st, Ctl* ctl, const Params& p, StateBufs sb, Lists L,
                  MeshDev mesh, double* forces) {
-  if (p.mixed)
+  if (p.mixed && p.pair_res)  // one evaluation per pair
+    launch_step_pairs<MixedPolicy, MixedPolicy::kMinBlocks, MixedPolicy::kMinBlocks>(
+        st, ctl, p, sb, L, mesh, forces);
+  else if (p.mixed)
     launch_step_warp<MixedPolicy>(st, ctl, p, sb, L, mesh, forces);
+  else if (p.mixed64)
+    launch_step_warp<Mixed64Policy>(st, ctl, p, sb, L, mesh, forces);
   else
     launch_step_fp64(st, ctl, p, sb, L, mesh, forces);
 }

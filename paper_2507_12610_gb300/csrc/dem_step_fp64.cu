@@ -94,7 +94,7 @@ struct Fp64Policy {
                                                   uint32_t stamp_new, LawOut<double>& o) {
     Geo g;
     if (!touch(p, Pi, Pj, g)) return false;
-    LawConst<double> cpp{p.Es_pp, p.Gs_pp, p.beta, p.mu_s, p.mu_r, p.mu_t, p.dt};
+    LawConst<double> cpp{p.Es_pp, p.Gs_pp, p.beta, p.mu_s, p.mu_r, p.mu_t, p.dt, p.cs_cn_pp};
     if (p.n_mat > 0) {  // the mean of the two materials' coefficients
       const D4 a = p.mat_d[(int)Wi.w], b = p.mat_d[(int)Wj.w];
       cpp.mu_s = (a.x + b.x) * 0.5;
@@ -103,6 +103,10 @@ struct Fp64Policy {
     }
     const V3<double> nh = (1.0 / g.dist) * g.d;
     const double Ri = Pi.w, Rj = Pj.w;
+    // the printed forms, in their order of operations: in a settled
+    // bed the per-particle torque sums cancel to a small fraction of their
+    // terms, so an algebraically equal form (R_i R_j / (R_i + R_j)) would
+    // amplify its last-bit differences past the 1e-12 bound
     const double Rs = 1.0 / (1.0 / Ri + 1.0 / Rj);
     const double ms = 1.0 / (1.0 / Vi.w + 1.0 / Vj.w);
     const double ri = Ri - g.delta / 2.0, rj = Rj - g.delta / 2.0;
@@ -113,7 +117,7 @@ struct Fp64Policy {
       ur = mk(h.ur[0], h.ur[1], h.ur[2]);
       ut = h.ut;
     }
-    o = contact_law(cpp, nh, g.delta, Rs, ms, ri, rj, 1.0 / ri + 1.0 / rj, xyz(Vi) - xyz(Vj),
+    o = contact_law(cpp, nh, g.delta, Rs, ms, ri, rj, 1.0 / (1.0 / ri + 1.0 / rj), xyz(Vi) - xyz(Vj),
                     ri * xyz(Wi) + rj * xyz(Wj), xyz(Wi) - xyz(Wj), us, ur, ut);
     h.us[0] = us.x; h.us[1] = us.y; h.us[2] = us.z;
     h.ur[0] = ur.x; h.ur[1] = ur.y; h.ur[2] = ur.z;
@@ -142,7 +146,7 @@ struct Fp64Policy {
     const double dist = sqrt(dot(d, d));
     const double delta = Pt.w + A.w - dist;
     if (delta < 0.0 || !(dist > 0.0)) return false;
-    LawConst<double> cpw{p.Es_pw, p.Gs_pw, p.beta, p.mu_s, p.mu_r, p.mu_t, p.dt};
+    LawConst<double> cpw{p.Es_pw, p.Gs_pw, p.beta, p.mu_s, p.mu_r, p.mu_t, p.dt, p.cs_cn_pw};
     if (p.n_mat > 0) {  // the particle's material
       const D4 a = p.mat_d[(int)Wt.w];
       cpw.mu_s = a.x;
@@ -164,7 +168,7 @@ struct Fp64Policy {
       ur = mk(h.ur[0], h.ur[1], h.ur[2]);
       ut = h.ut;
     }
-    const LawOut<double> o = contact_law(cpw, nh, delta, Pt.w, Vt.w, ri, 0.0, 1.0 / ri,
+    const LawOut<double> o = contact_law(cpw, nh, delta, Pt.w, Vt.w, ri, 0.0, 1.0 / (1.0 / ri),
                                          xyz(Vt) - vw, ri * xyz(Wt), xyz(Wt) - Om, us, ur, ut);
     HistD hn;
     hn.us[0] = us.x; hn.us[1] = us.y; hn.us[2] = us.z;
@@ -220,22 +224,18 @@ struct Fp64Policy {
     x = x + p.dt * v;
     const D4 q4 = Q[t];
     double q[4] = {q4.x, q4.y, q4.z, q4.w};
-    const double wn = sqrt(dot(w, w));
-    if (wn > 0.0) {
-      const double phi = p.dt / 2.0 * wn;
-      double sp, cp;
-      sincos(phi, &sp, &cp);
-      const double r[4] = {cp, sp * w.x / wn, sp * w.y / wn, sp * w.z / wn};
+    // q (cos phi, sin phi w^) with phi = dt |w| / 2 (pre-update w), then
+    // (cos th, sin th al^) with th = (dt / 2)^2 |al|
+    const double hw = p.dt / 2.0;
+    double r[4];
+    if (rot_factor(hw, w, r)) {
+      r[0] += 1.0;
       double o4[4];
       qmul(q, r, o4);
       q[0] = o4[0]; q[1] = o4[1]; q[2] = o4[2]; q[3] = o4[3];
     }
-    const double an = sqrt(dot(al, al));
-    if (an > 0.0) {
-      const double th = (p.dt / 2.0) * (p.dt / 2.0) * an;
-      double st, ct;
-      sincos(th, &st, &ct);
-      const double r[4] = {ct, st * al.x / an, st * al.y / an, st * al.z / an};
+    if (rot_factor(hw * hw, al, r)) {
+      r[0] += 1.0;
       double o4[4];
       qmul(q, r, o4);
       q[0] = o4[0]; q[1] = o4[1]; q[2] = o4[2]; q[3] = o4[3];

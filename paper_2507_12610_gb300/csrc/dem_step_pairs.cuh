@@ -34,6 +34,19 @@ template <>
 struct PairOut<double> {  // 80 bytes
   double f[3], ti[3], tj[3], pad;
 };
+template <>
+struct __align__(16) PairOut<float> {  // 48 bytes
+  float f[3], ti[3], tj[3], pad[3];
+};
+
+__device__ __forceinline__ void put_out(PairOut<float>* r, const LawOut<float>& o) {
+  PairOut<float> a;
+  a.f[0] = o.f.x; a.f[1] = o.f.y; a.f[2] = o.f.z;
+  a.ti[0] = o.ti.x; a.ti[1] = o.ti.y; a.ti[2] = o.ti.z;
+  a.tj[0] = o.tj.x; a.tj[1] = o.tj.y; a.tj[2] = o.tj.z;
+  a.pad[0] = a.pad[1] = a.pad[2] = 0.f;
+  *r = a;
+}
 
 __device__ __forceinline__ void put_out(PairOut<double>* r, const LawOut<double>& o) {
   PairOut<double> a;
@@ -44,8 +57,9 @@ __device__ __forceinline__ void put_out(PairOut<double>* r, const LawOut<double>
   *r = a;
 }
 // contribution to i (an upper entry) or to j (a lower entry)
-__device__ __forceinline__ void get_out(const PairOut<double>* r, bool on_i, double c6[6]) {
-  const double* t = on_i ? r->ti : r->tj;
+template <typename T>
+__device__ __forceinline__ void get_out(const PairOut<T>* r, bool on_i, T c6[6]) {
+  const T* t = on_i ? r->ti : r->tj;
   if (on_i) {
     c6[0] = r->f[0]; c6[1] = r->f[1]; c6[2] = r->f[2];
   } else {

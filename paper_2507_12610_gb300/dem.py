@@ -26,6 +26,7 @@ DEM_ERR_NOMEM = 6
 
 DEM_FP64 = 0
 DEM_MIXED = 1
+DEM_MIXED64 = 2
 
 _D = ctypes.c_double
 _I32 = ctypes.c_int32
@@ -36,7 +37,7 @@ _DP = ctypes.POINTER(ctypes.c_double)
 EXPORTS = ("dem_scene_create", "dem_step", "dem_synchronize", "dem_read_state",
            "dem_read_forces", "dem_read_contacts", "dem_get_stats", "dem_save", "dem_load",
            "dem_scene_destroy", "dem_status_string", "dem_step_timed",
-           "dem_contact_forces_noalloc", "dem_read_radii")
+           "dem_contact_forces_noalloc", "dem_read_radii", "dem_probe_fp64_fma")
 
 
 class dem_params(ctypes.Structure):
@@ -103,6 +104,7 @@ def load(path: str = LIB_PATH):
     lib.dem_load.argtypes = [P, P, ctypes.c_size_t]
     lib.dem_contact_forces_noalloc.argtypes = [ctypes.POINTER(dem_params), _I64, _D, P, P, P,
                                                P, P, P, P]
+    lib.dem_probe_fp64_fma.argtypes = [_I64, P, _DP]
     lib.dem_scene_destroy.argtypes = [P]
     lib.dem_scene_destroy.restype = None
     lib.dem_status_string.argtypes = [ctypes.c_int]
@@ -180,6 +182,15 @@ def contact_forces_noalloc(params: dict, n: int, r_max: float, R_ptr: int, x_ptr
                                               x_ptr, v_ptr, w_ptr, F_ptr, T_ptr, st))
 
 
+def probe_fp64_fma(iters: int = 16384, stream=None) -> float:
+    """FP64 FMA throughput of the current device (FMAs per second)."""
+    lib = load()
+    out = _D(0.0)
+    st = stream if stream is not None else current_stream()
+    _check(lib.dem_probe_fp64_fma(int(iters), st, ctypes.byref(out)), "dem_probe_fp64_fma")
+    return out.value
+
+
 def current_stream():
     """The current torch CUDA stream as a cudaStream_t (None if torch is absent)."""
     try:
@@ -203,6 +214,12 @@ class Scene:
         lib = load()
         self._lib = lib
         self._h = ctypes.c_void_p()
+        # kept for regrow(): the same scene with larger list capacities
+        self._init_args = (params, R, x, v, w, q, verts, tris, tri_radius, elems, elem_radius)
+        self._init_kw = dict(precision=precision, skin=skin, max_neighbors=max_neighbors,
+                             max_mesh_contacts=max_mesh_contacts, record_forces=record_forces,
+                             domain=domain, stream=stream, spawn=spawn, material=material,
+                             material_mu=material_mu, step_warps=step_warps)
         R = _f64(R, (-1,))
         n = R.shape[0]
         # rows: the given particles, then (with spawning) inactive rows up to n_max
@@ -286,6 +303,48 @@ class Scene:
 
     def step(self, nsteps: int = 1):
         _check(self._lib.dem_step(self._h, int(nsteps)), "dem_step")
+
+    # list capacities the library accepts (include/dem.h)
+    MAX_NEIGHBORS, MAX_MESH_CONTACTS = 64, 255
+
+    def regrow(self, factor: int = 2) -> None:
+        """Answer DEM_ERR_CAPACITY: the same scene with `factor` times the list
+        capacities (up to the library's limits), continuing from the last
+        completed step.  The step that overflowed did no work, so its state
+        and friction history are saved (dem_save), a scene with the larger
+        capacities is created and the blob loaded into it (dem_load)."""
+        blob = self.save()
+        kw = dict(self._init_kw)
+        cap = kw["max_neighbors"] if kw["max_neighbors"] > 0 else self.MAX_NEIGHBORS
+        capm = kw["max_mesh_contacts"] if kw["max_mesh_contacts"] > 0 else 16
+        kw["max_neighbors"] = min(self.MAX_NEIGHBORS, factor * cap)
+        kw["max_mesh_contacts"] = min(self.MAX_MESH_CONTACTS, factor * capm)
+        if (kw["max_neighbors"], kw["max_mesh_contacts"]) == (cap, capm):
+            raise DemError(DEM_ERR_CAPACITY, "regrow: capacities at the library's limit")
+        self.close()
+        self.__init__(*self._init_args, **kw)
+        self.load(blob)
+
+    def step_regrowing(self, nsteps: int, chunk: int = 256, max_regrows: int = 8) -> int:
+        """dem_step in chunks of `chunk` steps, checking the status after each;
+        a list overflow (DEM_ERR_CAPACITY) is answered by regrow() and the
+        steps that did no work are taken again.  Other errors raise.  Returns
+        the number of regrows."""
+        start = self.stats()["steps"]
+        regrows = 0
+        while True:
+            done = self.stats()["steps"] - start
+            if done >= nsteps:
+                return regrows
+            self.step(min(chunk, nsteps - done))
+            rc = self.synchronize()
+            if rc == DEM_ERR_CAPACITY:
+                if regrows >= max_regrows:
+                    raise DemError(rc, "step_regrowing: too many regrows")
+                self.regrow()
+                regrows += 1
+            elif rc != DEM_OK:
+                raise DemError(rc, "dem_step")
 
     def step_timed(self, nsteps: int) -> np.ndarray:
         """Run nsteps phase by phase; device ms of [mesh pose, rebuild, step, advance]."""

@@ -176,11 +176,14 @@ def lattice_box_scene(n_side=(10, 10, 10), seed=2, spacing=2.0e-3, r_range=(0.9e
     return _scene("lattice_box", seed, params, R, X, v, w, q, V, T, np.zeros(len(T)), (lo, hi))
 
 
-def column_scene(n=2000, seed=3, median=1.0e-3, sigma=0.2, gap=0.05e-3, spacing=None, **over):
+def column_scene(n=2000, seed=3, median=1.0e-3, sigma=0.2, gap=0.05e-3, spacing=None,
+                 walls=None, **over):
     """Square column of aspect ratio 2 (height = 2 x width) on a floor mesh.
 
     Particles sit on a jittered cubic lattice of pitch `spacing` (default
     2 R_max + gap: no overlaps); a smaller pitch gives initial contacts.
+    `walls` (optional) closes the floor with four vertical walls at +-walls
+    column widths from the axis, so no particle can leave it.
     """
     rng = np.random.default_rng(seed)
     rmin, rmax = median * math.exp(-3 * sigma), median * math.exp(3 * sigma)
@@ -207,6 +210,12 @@ def column_scene(n=2000, seed=3, median=1.0e-3, sigma=0.2, gap=0.05e-3, spacing=
     L = 6.0 * w_col
     V = np.array([[-L, -L, 0.0], [L, -L, 0.0], [L, L, 0.0], [-L, L, 0.0]])
     T = np.array([[0, 1, 2], [0, 2, 3]], dtype=np.int32)
+    if walls is not None:
+        W, H = walls * w_col, 2.5 * k * d
+        V = np.vstack([V, [[-W, -W, 0.0], [W, -W, 0.0], [W, W, 0.0], [-W, W, 0.0],
+                           [-W, -W, H], [W, -W, H], [W, W, H], [-W, W, H]]])
+        T = np.vstack([T, np.array([[4, 5, 9], [4, 9, 8], [5, 6, 10], [5, 10, 9],
+                                    [6, 7, 11], [6, 11, 10], [7, 4, 8], [7, 8, 11]])])
     v = np.zeros((n, 3))
     w = np.zeros((n, 3))
     q = _unit_quaternions(rng, n)
@@ -214,7 +223,7 @@ def column_scene(n=2000, seed=3, median=1.0e-3, sigma=0.2, gap=0.05e-3, spacing=
     params.update(over)
     lo = np.array([-L, -L, 0.0])
     hi = np.array([L, L, 2 * k * d + 2 * rmax])
-    return _scene("column", seed, params, R, X, v, w, q, V, T, np.zeros(2), (lo, hi))
+    return _scene("column", seed, params, R, X, v, w, q, V, T, np.zeros(len(T)), (lo, hi))
 
 
 def drum_geometry(n_particles, r_range=(0.8e-3, 1.2e-3), fill=0.35, packing=0.6):

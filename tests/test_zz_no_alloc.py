@@ -1,13 +1,17 @@
 """The allocation-free entry point dem_contact_forces_noalloc.
 
-It serves callers that must not allocate device memory (inside a stream
-capture, in a real-time loop, or when another allocator owns the device
-memory).  It evaluates the contact force and torque sums of a state without
-friction history, i.e. what the first step of a scene computes, using a fixed
-scratch array inside the library.  Checked through the C ABI against the
-existing path (dem_scene_create + dem_step(1) + dem_read_forces, DEM_FP64) at
-the FP64 tolerance of the other tests, on several calls in a row so the shared
-scratch array is reused.  This file is collected last on purpose.
+It serves callers that must not allocate device memory (a real-time loop,
+where an allocation can stall, or a host whose device memory belongs to
+another allocator).  It evaluates the contact force and torque sums of a
+state without friction history, i.e. what the first step of a scene
+computes, using a fixed scratch array inside the library.  Checked through
+the C ABI against the existing path (dem_scene_create + dem_step(1) +
+dem_read_forces, DEM_FP64) at the FP64 tolerance of the other tests, on
+several calls in a row so the shared scratch array is reused, and against the
+oracle's first step evaluated particle by particle.  Inputs it must refuse
+(radius above its bound, a particle outside the box, a crowded cell) are
+reported by the device and leave the next call unaffected.  This file is
+collected last on purpose.
 """
 import numpy as np
 import pytest
@@ -45,16 +49,19 @@ def reference_first_step(dem, s):
     return F, T
 
 
-def noalloc(torch, dem, s):
+def noalloc(torch, dem, s, rmax=None, box=None):
     dev = torch.device("cuda")
     n = len(s["R"])
     t = {k: torch.tensor(np.ascontiguousarray(s[k]), dtype=torch.float64, device=dev)
          for k in ("R", "x", "v", "w")}
     F = torch.empty((n, 3), dtype=torch.float64, device=dev)
     T = torch.empty((n, 3), dtype=torch.float64, device=dev)
-    rmax = float(s["R"].max())
-    lo = s["x"].min(axis=0) - 2 * rmax
-    hi = s["x"].max(axis=0) + 2 * rmax
+    rmax = float(s["R"].max()) if rmax is None else rmax
+    if box is None:
+        lo = s["x"].min(axis=0) - 2 * rmax
+        hi = s["x"].max(axis=0) + 2 * rmax
+    else:
+        lo, hi = box
     torch.cuda.synchronize()
     rc = dem.contact_forces_noalloc(s["params"], n, rmax, t["R"].data_ptr(), t["x"].data_ptr(),
                                     t["v"].data_ptr(), t["w"].data_ptr(), F.data_ptr(),
@@ -94,3 +101,46 @@ def test_noalloc_rejects_sizes_beyond_its_limit(env):
     rc = dem.contact_forces_noalloc(s["params"], 64, 1e-3, p, p, p, p, p, p,
                                     ((0, 0, 0), (1.0, 1.0, 1.0)))
     assert rc == dem.DEM_ERR_INVALID
+
+
+def test_noalloc_matches_the_oracle_first_step(env, oracle_mod):
+    # the oracle's first step (no friction history), particle by particle over
+    # all partners in ascending index, on a sample of the particles
+    torch, dem = env
+    s = scenes.lattice_box_scene((12, 12, 12), seed=34, spacing=1.95e-3, jitter=3e-5,
+                                 speed=0.05, spin=30.0, walls=False)
+    rc, F, T = noalloc(torch, dem, s)
+    assert rc == dem.DEM_OK, dem.status_string(rc)
+    ids = np.random.default_rng(3).choice(len(s["R"]), 300, replace=False)
+    o = oracle_mod.sample_first_step(s["params"], s["R"], s["x"], s["v"], s["w"], s["q"],
+                                     None, None, None, ids)
+    assert np.abs(o["F"]).max() > 0
+    assert rel(F[ids], o["F"]) <= TOL, rel(F[ids], o["F"])
+    assert rel(T[ids], o["T"]) <= TOL, rel(T[ids], o["T"])
+
+
+def test_noalloc_refuses_bad_inputs_on_the_device(env):
+    torch, dem = env
+    s = scenes.lattice_box_scene((6, 6, 6), seed=35, spacing=1.95e-3, speed=0.05, spin=10.0,
+                                 walls=False)
+    rmax = float(s["R"].max())
+    # a radius above the stated bound
+    rc, _, _ = noalloc(torch, dem, s, rmax=0.5 * rmax)
+    assert rc == dem.DEM_ERR_INVALID
+    # a particle outside the box
+    lo = s["x"].min(axis=0) - 2 * rmax
+    hi = s["x"].max(axis=0) + 2 * rmax
+    bad = dict(s, x=s["x"].copy())
+    bad["x"][7] = hi + 0.01
+    rc, _, _ = noalloc(torch, dem, bad, box=(lo, hi))
+    assert rc == dem.DEM_ERR_INVALID
+    # more particles in one cell than the scratch allows
+    crowd = dict(s, x=s["x"].copy())
+    crowd["x"][:80] = s["x"][0] + np.random.default_rng(1).uniform(-1e-4, 1e-4, (80, 3))
+    rc, _, _ = noalloc(torch, dem, crowd)
+    assert rc == dem.DEM_ERR_CAPACITY
+    # the next call starts from a clear status and gives the reference forces
+    F_ref, T_ref = reference_first_step(dem, s)
+    rc, F, T = noalloc(torch, dem, s)
+    assert rc == dem.DEM_OK
+    assert rel(F, F_ref) <= TOL and rel(T, T_ref) <= TOL
