@@ -451,6 +451,34 @@ def bench_ours(a):
                        "mesh_contacts": st64["mesh_contacts"]}
         sd.close()
 
+    # DEM_MIXED64 beside it: the FP32 contact law with FP64 state
+    if prec == dem.DEM_MIXED:
+        k2 = max(20, a.steps)
+        with torch.cuda.stream(strm):
+            s2 = dem.Scene.from_dict(s_set, precision=dem.DEM_MIXED64, skin=a.skin)
+        s2.step(max(3, a.warmup))
+        s2.synchronize()
+        barrier()
+        e0.record(strm)
+        s2.step(k2)
+        e1.record(strm)
+        e1.synchronize()
+        rc2 = s2.synchronize()
+        t2 = rank_max(e0.elapsed_time(e1) / 1e3)
+        k_ph2 = max(10, k2 // 4)
+        ph2 = s2.step_timed(k_ph2)
+        st2b = s2.stats()
+        kms2 = ph2[2] / k_ph2
+        b2 = algorithmic_bytes(n, st2b, True) + 4 * n  # radius read as a double
+        out["mixed64"] = {"value": aggregate_rate(n, k2, t2, world), "ms_per_step": t2 / k2 * 1e3,
+                          "steps": k2, "status": rc2, "step_kernel_ms": kms2,
+                          "precision": "FP32 contact law and springs, FP64 positions, "
+                                       "velocities, spins and orientations",
+                          "hbm": {"achieved": b2 / (kms2 * 1e-3) / 1e9, "peak": peaks["hbm_gbs"],
+                                  "unit": "GB/s",
+                                  "frac": b2 / (kms2 * 1e-3) / 1e9 / peaks["hbm_gbs"]}}
+        s2.close()
+
     # end to end through the C ABI with host buffers: create from host arrays
     # (H2D), step in frames, read the full state back after every frame (D2H)
     if not a.no_e2e:
@@ -524,8 +552,9 @@ def bench_batch(a, dem, strm, barrier, rank_max, world):
     st = sc.state()
     sc.close()
     b = dict(b, x=st["x"], v=st["v"], w=st["w"], q=st["q"])
-    best, table = batch.autotune(b, precision=dem.DEM_MIXED, skins=[0.2e-3, 0.4e-3],
-                                 steps=100, warmup=20, dem=dem)
+    best, table = batch.autotune(b, precision=dem.DEM_MIXED,
+                                 skins=[0.2e-3, 0.3e-3, 0.45e-3, 0.6e-3], steps=100, warmup=20,
+                                 dem=dem)
     with torch.cuda.stream(strm):
         sc = dem.Scene.from_dict(b, precision=dem.DEM_MIXED, skin=best["skin"],
                                  step_warps=best["step_warps"])
@@ -544,6 +573,13 @@ def bench_batch(a, dem, strm, barrier, rank_max, world):
     t = rank_max(e0.elapsed_time(e1) / 1e3)
     st = sc.stats()
     f = batch.discharged(b, sc.state()["x"])
+    # the step kernel's roofline on the batch (phase-timed steps after the run)
+    k_ph = 50
+    ph = sc.step_timed(k_ph)
+    stb = sc.stats()
+    kms = ph[2] / k_ph
+    bytes_b = algorithmic_bytes(n, stb, True)
+    peaks, _ = measured_peaks()
     sc.close()
     return {"value": aggregate_rate(n, k, t, world), "unit": UNIT, "ms_per_step": t / k * 1e3,
             "steps": k, "status": rc, "n_scenes": a.batch_scenes, "n_particles": n,
@@ -556,25 +592,44 @@ def bench_batch(a, dem, strm, barrier, rank_max, world):
             "rebuilds_in_timed": st["rebuilds"] - st0["rebuilds"],
             "pair_contacts": st["pair_contacts"], "mesh_contacts": st["mesh_contacts"],
             "contacts_per_s": (st["pair_contacts"] + st["mesh_contacts"]) * k * world / t,
-            "discharged_fraction_median": float(np.median(f))}
+            "discharged_fraction_median": float(np.median(f)),
+            "roofline": {"bound": "hbm", "kernel": "k_step_warp<MixedPolicy>",
+                         "kernel_ms": kms, "algorithmic_bytes_per_launch": bytes_b,
+                         "achieved": bytes_b / (kms * 1e-3) / 1e9, "peak": peaks["hbm_gbs"],
+                         "unit": "GB/s",
+                         "frac": bytes_b / (kms * 1e-3) / 1e9 / peaks["hbm_gbs"]}}
 
 
 def bench_surrogate(dem, strm, n=100_000):
+    """The learned surrogate on the 100,000-sphere drum: trained briefly on the
+    DEM's own hopper trajectories, then timed per 10-step stride (cell-list
+    graph + forward, device) against 10 DEM steps, with the position error of
+    one network stride and of a 3-stride run with DEM fallback."""
     import torch
-    from paper_2507_12610_gb300 import scenes, surrogate
+    from paper_2507_12610_gb300 import batch, scenes, surrogate
+    rng = np.random.default_rng(3)
+    b = batch.combine([batch.hopper_scene(int(m), 900 + k,
+                                          (float(rng.uniform(0.2, 0.8)), 0.1, 0.1))
+                       for k, m in enumerate((900, 1400, 2000, 2800))])
+    t0 = time.perf_counter()
+    pairs, Rb = surrogate.sample_pairs(b, 16, every=100, settle=2000)
+    model = surrogate.MPNN(seed=0)
+    surrogate.train(model, pairs, Rb, b["params"]["dt"], iters=400, lr=1e-3, lr_end=1e-4,
+                    log_every=400)
+    t_train = time.perf_counter() - t0
     d = scenes.drum_scene(n=n, seed=5, nn_dist=2.15e-3, speed=0.02,
                           radius=scenes.drum_geometry(n)[0])
     with torch.cuda.stream(strm):
         sc = dem.Scene.from_dict(d, precision=dem.DEM_MIXED)
-    sc.step(500)
+    sc.step(1500)
     st = sc.state()
+    sc.step(20)
     sc.synchronize()
     t0 = time.perf_counter()
     sc.step(100)
     sc.synchronize()
     dem_ms = (time.perf_counter() - t0) * 1e3 / 10
     sc.close()
-    model = surrogate.MPNN(seed=0)
     surrogate.predict(model, st, d["R"])  # warm-up
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -583,11 +638,21 @@ def bench_surrogate(dem, strm, n=100_000):
         surrogate.predict(model, st, d["R"])
     torch.cuda.synchronize()
     net_ms = (time.perf_counter() - t0) * 1e3 / k
+    surrogate._mesh_kw.clear()
+    surrogate._mesh_kw.update(verts=d["verts"], tris=d["tris"], tri_radius=d["tri_radius"])
+    one = surrogate.rollout(model, st, d["R"], d["params"], 1, overlap_growth=1e9,
+                            energy_limit=1e9)
+    hyb = surrogate.rollout(model, st, d["R"], d["params"], 3)
     return {"value": n * 10 / (net_ms * 1e-3), "unit": UNIT, "n_particles": n,
             "stride_steps": 10, "ms_per_stride": net_ms, "dem_ms_per_stride": dem_ms,
             "gain": dem_ms / net_ms,
-            "note": "network time (all-pairs graph + 3-round MPNN, bf16) per 10-step stride; "
-                    "its trajectory error is measured by paper_2507_12610_gb300.surrogate"}
+            "pos_error_one_stride_rms_over_rmax": one["pos_error_rms_over_rmax"][0][1],
+            "hybrid_3_strides": {"fallbacks": hyb["fallbacks"],
+                                 "pos_error_rms_over_rmax": [e for _, e, _ in
+                                                             hyb["pos_error_rms_over_rmax"]]},
+            "train_s": t_train, "train_pairs": 16, "train_iters": 400,
+            "note": "trained network (cell-list graph + 3-round MPNN, bf16 weights, fp32 "
+                    "accumulation) per 10-step stride against 10 DEM_MIXED steps"}
 
 
 def oracle_sample(seed: int = 5):

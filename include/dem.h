@@ -179,7 +179,10 @@ typedef struct dem_stats {
 typedef struct dem_scene dem_scene;
 
 /* Create a scene on the current CUDA device.  `stream` is a cudaStream_t (NULL:
- * the library creates its own).  Copies the host arrays to the device.
+ * the library creates its own).  Copies the host arrays to the device (the
+ * particle state of Sec. 2.1 / Table 3, the mesh elements of Sec. 3.3) and
+ * captures the step sequence into CUDA graphs (1 and 16 steps, for a start
+ * at an even and at an odd step), which dem_step replays.
  * Errors: DEM_ERR_INVALID (parameters outside Table 2's requirements, n < 1,
  * non-finite input, bad element), DEM_ERR_NOMEM, DEM_ERR_CUDA. */
 int dem_scene_create(const dem_params* params, const dem_particles* particles,

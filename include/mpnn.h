@@ -58,6 +58,18 @@ int mpnn_graph(int64_t n, const float* x, float cutoff, int64_t* cnt, int64_t* o
                int32_t* nbr, int32_t* dst, int64_t max_edges, int64_t* n_edges_host,
                void* stream);
 
+/* The same graph from cell lists (cells of edge `cutoff` over the nodes'
+ * bounding box, 27 cells searched per node; O(n)), in ascending j per node.
+ * work: device workspace of 2 (max_cells + 1) + 2 n int64 words + 1; box:
+ * 6 floats of device memory (the bounding box, written).  The call waits for
+ * the bounding box and the edge count.  Errors: DEM_ERR_INVALID (n < 1 or
+ * n >= 2^24, non-finite positions, cutoff <= 0), DEM_ERR_CAPACITY (more than
+ * max_cells cells, more than max_edges edges, or a node with more than 128
+ * neighbours; nothing written then). */
+int mpnn_graph_cells(int64_t n, const float* x, float cutoff, int64_t max_cells, int64_t* work,
+                     float* box, int64_t* cnt, int64_t* off, int32_t* nbr, int32_t* dst,
+                     int64_t max_edges, int64_t* n_edges_host, void* stream);
+
 /* perm[k] = index of the reverse of edge k (the graph is symmetric); grouped
  * by off, perm lists the edges each node sends, in ascending receiver. */
 int mpnn_reverse_edges(int64_t E, const int64_t* off, const int32_t* nbr, const int32_t* dst,

@@ -501,7 +501,7 @@ int install_contacts(dem_scene* s, const std::vector<ContactRow>& rows, uint32_t
   offs[0] = 0;
   for (int64_t i = 0; i < n; ++i) offs[i + 1] = offs[i] + (uint32_t)pp[i].size();
   const size_t E = offs[n];
-  std::vector<uint32_t> nbr(E);
+  std::vector<uint32_t> nbr(E);  // slot = caller index here, so also the partner keys
   std::vector<unsigned char> hpp(E * s->hist_bytes), hpm(maxnt * n * s->hist_bytes);
   auto encode = [&](const ContactRow& r, unsigned char* rec) {
     if (s->p.hist32) {
@@ -537,6 +537,7 @@ int install_contacts(dem_scene* s, const std::vector<ContactRow>& rows, uint32_t
   DEM_TRY(cudaMemcpy(lb.offs, offs.data(), (n + 1) * 4, cudaMemcpyHostToDevice));
   if (E) {
     DEM_TRY(cudaMemcpy(lb.nbr, nbr.data(), nbr.size() * 4, cudaMemcpyHostToDevice));
+    DEM_TRY(cudaMemcpy(lb.ngid, nbr.data(), nbr.size() * 4, cudaMemcpyHostToDevice));
     DEM_TRY(cudaMemcpy(lb.hpp, hpp.data(), hpp.size(), cudaMemcpyHostToDevice));
   }
   if (maxnt) {
@@ -907,6 +908,7 @@ int dem_scene_create(const dem_params* params, const dem_particles* parts, const
     lb.meta = M.get<uint32_t>(n);
     lb.offs = M.get<uint32_t>(n + 1);
     lb.nbr = M.get<uint32_t>((size_t)p.cap * n);
+    lb.ngid = M.get<uint32_t>((size_t)p.cap * n);
     lb.hpp = M.get<unsigned char>((size_t)p.cap * n * s->hist_bytes);
     if (one_eval_per_pair(p)) {
       lb.mir = M.get<uint32_t>((size_t)p.cap * n);
@@ -925,6 +927,7 @@ int dem_scene_create(const dem_params* params, const dem_particles* parts, const
   s->bb.cell_start = M.get<uint32_t>(ncells + 2);
   s->bb.block_sums = M.get<uint32_t>(scan_block_sums_size(std::max<int64_t>(ncells + 1, n)) + 1);
   s->bb.tmp_nbr = M.get<uint32_t>((size_t)p.cap * n);
+  s->bb.tmp_gid = M.get<uint32_t>((size_t)p.cap * n);
   s->bb.tmp_cnt = M.get<uint32_t>(n);
   s->bb.tmp_offs = M.get<uint32_t>(n + 1);
   if (p.record_forces) s->forces = M.get<double>(6 * (size_t)n);
@@ -1066,6 +1069,16 @@ int dem_scene_create(const dem_params* params, const dem_particles* parts, const
   launch_mesh_pose(s->stream, s->ctl, s->p, mesh_at(s->mesh, 0), 0);
   launch_mesh_pose(s->stream, s->ctl, s->p, mesh_at(s->mesh, 1), 1);
   if (cudaStreamSynchronize(s->stream) != cudaSuccess) return fail(DEM_ERR_CUDA);
+  // capture and instantiate the step graphs now (1 and kGraphSteps steps,
+  // both parities), so that no dem_step call pays for it on the host while
+  // the device waits; a failure here leaves them to be built on first use
+  for (int odd = 0; odd < 2; ++odd) {
+    if (!s->exec1[odd] && build_graph(s, 1, odd, &s->exec1[odd]) != DEM_OK)
+      s->exec1[odd] = nullptr;
+    if (!s->execG[odd] && build_graph(s, kGraphSteps, odd, &s->execG[odd]) != DEM_OK)
+      s->execG[odd] = nullptr;
+  }
+  cudaGetLastError();
   *out = s;
   return DEM_OK;
 }

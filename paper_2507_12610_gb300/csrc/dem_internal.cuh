@@ -148,6 +148,7 @@ struct ListBuf {
   uint32_t* meta;   // [n] list length | lower-id count << 8 | triangle count << 16
   uint32_t* offs;   // [n + 1] CSR offsets of the pair entries (slot order)
   uint32_t* nbr;    // [offs[n]] partner slots, ascending partner caller index per particle
+  uint32_t* ngid;   // [offs[n]] partner caller indices (the keys of the history remap)
   void* hpp;        // [offs[n]] pair history (HistD or HistM), one record per entry
   uint32_t* tric;   // [capm][n] candidate triangles, ascending
   void* hpm;        // [capm][n] triangle history
@@ -192,6 +193,7 @@ struct BinBuf {
   uint32_t* order;      // [n] old slot of each new slot
   uint32_t* block_sums; // scan partials
   uint32_t* tmp_nbr;    // [cap][n] candidates of the list being built (slot order)
+  uint32_t* tmp_gid;    // [cap][n] their caller indices
   uint32_t* tmp_cnt;    // [n] their counts
   uint32_t* tmp_offs;   // [n + 1] exclusive prefix of the counts
   // triangle cell lists
@@ -246,6 +248,7 @@ __device__ __forceinline__ ListBuf list_of(const Lists& L, uint32_t b) {
   r.meta = b ? L.b[1].meta : L.b[0].meta;
   r.offs = b ? L.b[1].offs : L.b[0].offs;
   r.nbr = b ? L.b[1].nbr : L.b[0].nbr;
+  r.ngid = b ? L.b[1].ngid : L.b[0].ngid;
   r.hpp = b ? L.b[1].hpp : L.b[0].hpp;
   r.tric = b ? L.b[1].tric : L.b[0].tric;
   r.hpm = b ? L.b[1].hpm : L.b[0].hpm;

@@ -124,6 +124,13 @@ __global__ void k_advance(Ctl* ctl, Params p) {
 // ============================================================================
 
 __device__ __forceinline__ V3<float> hi3(float4 a) { return mk(a.x, a.y, a.z); }
+// r_i w_i + r_j w_j with rounded products and a commutative sum (no
+// contraction): the same bits whichever body comes first
+__device__ __forceinline__ V3<float> sym_sum(float ri, V3<float> wi, float rj, V3<float> wj) {
+  return mk(__fadd_rn(__fmul_rn(ri, wi.x), __fmul_rn(rj, wj.x)),
+            __fadd_rn(__fmul_rn(ri, wi.y), __fmul_rn(rj, wj.y)),
+            __fadd_rn(__fmul_rn(ri, wi.z), __fmul_rn(rj, wj.z)));
+}
 // accurate difference of two hi/lo 3-vectors, rounded once
 __device__ __forceinline__ V3<float> diff3(const F8& a, const F8& b) {
   return mk((a.hi.x - b.hi.x) + (a.lo.x - b.lo.x), (a.hi.y - b.hi.y) + (a.lo.y - b.lo.y),
@@ -337,7 +344,7 @@ struct MixedPolicy {
       ut = h.ut;
     }
     o = contact_law(cpp, g.n, g.delta, Rs, ms, ri, rj, ri * rj / (ri + rj), diff3(Vi, Vj),
-                    ri * sum3(Wi) + rj * sum3(Wj), diff3(Wi, Wj), us, ur, ut);
+                    sym_sum(ri, sum3(Wi), rj, sum3(Wj)), diff3(Wi, Wj), us, ur, ut);
     h.us[0] = us.x; h.us[1] = us.y; h.us[2] = us.z;
     h.ur[0] = ur.x; h.ur[1] = ur.y; h.ur[2] = ur.z;
     h.ut = ut;
@@ -594,8 +601,8 @@ struct Mixed64Policy {
     const V3<float> wj = mk((float)Wj.x, (float)Wj.y, (float)Wj.z);
     const V3<float> dv = mk((float)(Vi.x - Vj.x), (float)(Vi.y - Vj.y), (float)(Vi.z - Vj.z));
     const V3<float> om = mk((float)(Wi.x - Wj.x), (float)(Wi.y - Wj.y), (float)(Wi.z - Wj.z));
-    o = contact_law(cpp, nh, delta, Rs, ms, ri, rj, ri * rj / (ri + rj), dv, ri * wi + rj * wj,
-                    om, us, ur, ut);
+    o = contact_law(cpp, nh, delta, Rs, ms, ri, rj, ri * rj / (ri + rj), dv,
+                    sym_sum(ri, wi, rj, wj), om, us, ur, ut);
     h.us[0] = us.x; h.us[1] = us.y; h.us[2] = us.z;
     h.ur[0] = ur.x; h.ur[1] = ur.y; h.ur[2] = ur.z;
     h.ut = ut;

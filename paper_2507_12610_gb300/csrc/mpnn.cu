@@ -312,6 +312,126 @@ k_graph(int64_t n, const float* __restrict__ x, float cut2, int pass,
   if (pass == 0 && i < n) cnt_or_off[i] = k;
 }
 
+// ---- neighbour graph from cell lists (cells of edge = cutoff) ---------------
+
+constexpr int kMaxDegree = 128;  // neighbours of one node within the cutoff
+
+// Bounding box of the nodes (one block): box = (lo xyz, hi xyz).
+__global__ void __launch_bounds__(1024) k_box(int64_t n, const float* __restrict__ x,
+                                              float* __restrict__ box) {
+  __shared__ float s[6][1024];
+  float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x)
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = fminf(lo[a], x[3 * i + a]);
+      hi[a] = fmaxf(hi[a], x[3 * i + a]);
+    }
+  for (int a = 0; a < 3; ++a) {
+    s[a][threadIdx.x] = lo[a];
+    s[3 + a][threadIdx.x] = hi[a];
+  }
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o)
+      for (int a = 0; a < 3; ++a) {
+        s[a][threadIdx.x] = fminf(s[a][threadIdx.x], s[a][threadIdx.x + o]);
+        s[3 + a][threadIdx.x] = fmaxf(s[3 + a][threadIdx.x], s[3 + a][threadIdx.x + o]);
+      }
+    __syncthreads();
+  }
+  if (threadIdx.x < 6) box[threadIdx.x] = s[threadIdx.x][0];
+}
+
+struct CellGrid {
+  float lo[3];
+  float inv_h;
+  int32_t nc[3];
+};
+
+__device__ __forceinline__ int3 grid_cell(const CellGrid& g, float x, float y, float z) {
+  const float p[3] = {x, y, z};
+  int c[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    int ci = (int)floorf((p[a] - g.lo[a]) * g.inv_h);
+    c[a] = ci < 0 ? 0 : (ci >= g.nc[a] ? g.nc[a] - 1 : ci);
+  }
+  return make_int3(c[0], c[1], c[2]);
+}
+
+// cell of every node and its arrival index in the cell
+__global__ void k_cells_count(int64_t n, const float* __restrict__ x, CellGrid g,
+                              unsigned long long* __restrict__ ccount,
+                              int64_t* __restrict__ keyloc) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int3 c = grid_cell(g, x[3 * i], x[3 * i + 1], x[3 * i + 2]);
+    const int64_t key = ((int64_t)c.z * g.nc[1] + c.y) * g.nc[0] + c.x;
+    const unsigned long long loc = atomicAdd(&ccount[key], 1ull);
+    keyloc[i] = (key << 24) | (int64_t)loc;
+  }
+}
+
+__global__ void k_cells_scatter(int64_t n, const int64_t* __restrict__ keyloc,
+                                const int64_t* __restrict__ cstart, int32_t* __restrict__ order) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t kl = keyloc[i];
+    order[cstart[kl >> 24] + (kl & 0xffffff)] = (int32_t)i;
+  }
+}
+
+// pass 0 counts (and records the largest degree), pass 1 writes: for node i,
+// its neighbours j != i with |x_j - x_i| < cut from the 27 cells around it,
+// in ascending j, and dst of each edge.
+__global__ void __launch_bounds__(128)
+k_graph_cells(int64_t n, const float* __restrict__ x, CellGrid g, float cut2, int pass,
+              const int64_t* __restrict__ cstart, const int32_t* __restrict__ order,
+              int64_t* __restrict__ cnt_or_off, int32_t* __restrict__ nbr,
+              int32_t* __restrict__ dst, unsigned int* __restrict__ max_degree) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float xi = x[3 * i], yi = x[3 * i + 1], zi = x[3 * i + 2];
+  const int3 c = grid_cell(g, xi, yi, zi);
+  int32_t found[kMaxDegree];
+  int k = 0;
+  for (int dz = -1; dz <= 1; ++dz) {
+    const int cz = c.z + dz;
+    if (cz < 0 || cz >= g.nc[2]) continue;
+    for (int dy = -1; dy <= 1; ++dy) {
+      const int cy = c.y + dy;
+      if (cy < 0 || cy >= g.nc[1]) continue;
+      const int x0 = c.x > 0 ? c.x - 1 : 0, x1 = c.x + 1 < g.nc[0] ? c.x + 1 : g.nc[0] - 1;
+      const int64_t row = ((int64_t)cz * g.nc[1] + cy) * g.nc[0];
+      for (int64_t s = cstart[row + x0]; s < cstart[row + x1 + 1]; ++s) {
+        const int32_t j = order[s];
+        if ((int64_t)j == i) continue;
+        const float dx = x[3 * j] - xi, dy2 = x[3 * j + 1] - yi, dz2 = x[3 * j + 2] - zi;
+        if (dx * dx + dy2 * dy2 + dz2 * dz2 >= cut2) continue;
+        if (pass == 1 && k < kMaxDegree) {  // sorted insertion (ascending j)
+          int m = k;
+          while (m > 0 && found[m - 1] > j) {
+            found[m] = found[m - 1];
+            --m;
+          }
+          found[m] = j;
+        }
+        ++k;
+      }
+    }
+  }
+  if (pass == 0) {
+    cnt_or_off[i] = k;
+    atomicMax(max_degree, (unsigned int)k);
+  } else {
+    const int64_t base = cnt_or_off[i];
+    for (int m = 0; m < k && m < kMaxDegree; ++m) {
+      nbr[base + m] = found[m];
+      dst[base + m] = (int32_t)i;
+    }
+  }
+}
+
 // Exclusive scan of n counts into off[0..n] by one block (ascending).
 __global__ void k_scan_counts(int64_t n, const int64_t* __restrict__ cnt, int64_t* __restrict__ off) {
   __shared__ int64_t part[1024];
@@ -561,6 +681,61 @@ int mpnn_graph(int64_t n, const float* x, float cutoff, int64_t* cnt, int64_t* o
   if (n_edges_host) *n_edges_host = E;
   if (E > max_edges || !nbr || !dst) return E > max_edges ? DEM_ERR_CAPACITY : DEM_ERR_INVALID;
   k_graph<<<nb, 256, 0, st>>>(n, x, c2, 1, off, nbr, dst);
+  return launch_status();
+}
+
+int mpnn_graph_cells(int64_t n, const float* x, float cutoff, int64_t max_cells, int64_t* work,
+                     float* box, int64_t* cnt, int64_t* off, int32_t* nbr, int32_t* dst,
+                     int64_t max_edges, int64_t* n_edges_host, void* stream) {
+  if (n <= 0 || n >= ((int64_t)1 << 24) || !x || !(cutoff > 0) || max_cells <= 0 || !work ||
+      !box || !cnt || !off)
+    return DEM_ERR_INVALID;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  k_box<<<1, 1024, 0, st>>>(n, x, box);
+  float hb[6];
+  if (cudaMemcpyAsync(hb, box, sizeof hb, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return DEM_ERR_CUDA;
+  CellGrid g;
+  int64_t ncells = 1;
+  for (int a = 0; a < 3; ++a) {
+    if (!(hb[a] <= hb[3 + a])) return DEM_ERR_INVALID;  // non-finite positions
+    g.lo[a] = hb[a];
+    const double ext = (double)hb[3 + a] - (double)hb[a];
+    const int64_t c = (int64_t)(ext / cutoff) + 1;
+    g.nc[a] = (int32_t)(c < (1 << 20) ? c : (1 << 20));
+    ncells *= g.nc[a];
+    if (ncells > max_cells) return DEM_ERR_CAPACITY;
+  }
+  g.inv_h = 1.f / cutoff;
+  // workspace: cell counts [ncells + 1], cell starts [ncells + 1], key|local [n], order [n]
+  unsigned long long* ccount = reinterpret_cast<unsigned long long*>(work);
+  int64_t* cstart = work + (max_cells + 1);
+  int64_t* keyloc = cstart + (max_cells + 1);
+  int32_t* order = reinterpret_cast<int32_t*>(keyloc + n);
+  unsigned int* maxdeg = reinterpret_cast<unsigned int*>(order + n);
+  if (cudaMemsetAsync(ccount, 0, sizeof(int64_t) * (ncells + 1), st) != cudaSuccess ||
+      cudaMemsetAsync(maxdeg, 0, sizeof(unsigned int), st) != cudaSuccess)
+    return DEM_ERR_CUDA;
+  const unsigned nb = grid_for(n, 256);
+  k_cells_count<<<nb, 256, 0, st>>>(n, x, g, ccount, keyloc);
+  k_scan_counts<<<1, 1024, 0, st>>>(ncells, reinterpret_cast<const int64_t*>(ccount), cstart);
+  k_cells_scatter<<<nb, 256, 0, st>>>(n, keyloc, cstart, order);
+  const float c2 = cutoff * cutoff;
+  const unsigned nb128 = (unsigned)((n + 127) / 128);
+  k_graph_cells<<<nb128, 128, 0, st>>>(n, x, g, c2, 0, cstart, order, cnt, nullptr, nullptr,
+                                       maxdeg);
+  k_scan_counts<<<1, 1024, 0, st>>>(n, cnt, off);
+  int64_t E = 0;
+  unsigned int md = 0;
+  if (cudaMemcpyAsync(&E, off + n, sizeof E, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaMemcpyAsync(&md, maxdeg, sizeof md, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return DEM_ERR_CUDA;
+  if (n_edges_host) *n_edges_host = E;
+  if (md > (unsigned)kMaxDegree) return DEM_ERR_CAPACITY;
+  if (E > max_edges || !nbr || !dst) return E > max_edges ? DEM_ERR_CAPACITY : DEM_ERR_INVALID;
+  k_graph_cells<<<nb128, 128, 0, st>>>(n, x, g, c2, 1, cstart, order, off, nbr, dst, maxdeg);
   return launch_status();
 }
 

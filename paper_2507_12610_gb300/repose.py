@@ -81,8 +81,15 @@ def main():
     ap.add_argument("--seed", type=int, default=7)
     ap.add_argument("--max-time", type=float, default=20.0)
     ap.add_argument("--ke", action="store_true", help="keep the kinetic-energy history")
+    ap.add_argument("--gap", type=float, default=11, help="plate gap in grain diameters")
+    ap.add_argument("--dt-div", type=float, default=10.0, help="time step = Eq. dt / this")
+    ap.add_argument("--spawn-angle", type=float, default=60.0,
+                    help="the spawn box sits above the heap of this angle (deg)")
+    ap.add_argument("--v0", type=float, default=-0.5, help="vertical speed of spawned grains")
     a = ap.parse_args()
-    r = run(a.n, 0 if a.precision == "fp64" else 1, a.seed, a.max_time)
+    r = run(a.n, 0 if a.precision == "fp64" else 1, a.seed, a.max_time, gap_diameters=a.gap,
+            dt_div=a.dt_div, spawn_angle=a.spawn_angle, v0=a.v0)
+    r.update(gap=a.gap, dt_div=a.dt_div, spawn_angle=a.spawn_angle, v0=a.v0)
     if not a.ke:
         r.pop("ke_history")
     print(json.dumps(r))

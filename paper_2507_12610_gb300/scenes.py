@@ -372,17 +372,19 @@ def _box_rect(x0, x1, y0, y1, z0, z1):
 
 
 def repose_scene(n=20_000, seed=7, R=1.0e-3, gap_diameters=11, stream_diameters=6,
-                 mu_s=3.0, mu_r=3.0, attempts=64, every=10, v0=-0.5, **over):
+                 mu_s=3.0, mu_r=3.0, attempts=64, every=10, v0=-0.5, dt_div=10.0,
+                 spawn_angle=60.0, **over):
     """Quasi-2D heap between two vertical plates (the piling example, Sec. 5).
 
     Monodisperse grains of radius R between plates gap_diameters diameters
     apart (y), with the material defaults of Table 2 (rho 1000, E 1 MPa, nu 0.3,
     e_n 0.5), the strong friction mu_s = mu_r = 3, mu_t = 2 mu_s / 3 (Table 2's
-    default rule), and a time step ten times below Eq. dt.  As in the paper, a
-    stream of spawned grains piles up: the spawn box spans the gap, is
+    default rule), and a time step dt_div = 10 times below Eq. dt.  As in the
+    paper, a stream of spawned grains piles up: the spawn box spans the gap, is
     stream_diameters wide in x and sits above the height of the final heap for
-    angles up to 60 degrees; it gets `attempts` attempts every `every` steps,
-    the grains start with vertical velocity v0, until n grains are in.  The
+    angles up to spawn_angle degrees; it gets `attempts` attempts every `every`
+    steps, the grains start with vertical velocity v0, until n grains are in.
+    The
     floor and the two end walls are far outside the heap's base.  All mesh
     elements are rectangles of radius 0.
     """
@@ -391,9 +393,10 @@ def repose_scene(n=20_000, seed=7, R=1.0e-3, gap_diameters=11, stream_diameters=
     hy = 0.5 * W
     area = n * (math.pi / 6.0) * d ** 3 / (0.6 * W)  # heap cross-section at packing 0.6
     h60 = math.sqrt(area * math.tan(math.radians(60.0)))
+    h_sp = math.sqrt(area * math.tan(math.radians(spawn_angle)))
     base40 = 2.0 * math.sqrt(area * math.tan(math.radians(40.0))) / math.tan(math.radians(40.0))
     half_floor = 0.8 * base40 + 5 * d
-    z_sp = 1.1 * h60 + 8 * d
+    z_sp = 1.1 * h_sp + 8 * d
     top = z_sp + 8 * d
     rects = [
         _box_rect(-half_floor, half_floor, -hy, hy, 0.0, 0.0),            # floor
@@ -405,7 +408,7 @@ def repose_scene(n=20_000, seed=7, R=1.0e-3, gap_diameters=11, stream_diameters=
     V = np.array([p for r in rects for p in r], dtype=np.float64)
     E = np.arange(4 * len(rects), dtype=np.int32).reshape(-1, 4)
     params = base_params(rho=1000.0, E=1.0e6, nu=0.3, e_n=0.5, mu_s=mu_s, mu_r=mu_r,
-                         mu_t=2.0 * mu_s / 3.0, dt=eq_dt(R, 1000.0, 0.3, 1.0e6) / 10.0)
+                         mu_t=2.0 * mu_s / 3.0, dt=eq_dt(R, 1000.0, 0.3, 1.0e6) / dt_div)
     params.update(over)
     half_stream = 0.5 * stream_diameters * d
     spawn = dict(n_max=n, lo=(-half_stream, -hy + R, z_sp), hi=(half_stream, hy - R, z_sp + 4 * d),

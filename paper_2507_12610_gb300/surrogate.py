@@ -27,7 +27,7 @@ import numpy as np
 from . import dem as _dem
 
 EXPORTS = ("mpnn_gemm", "mpnn_gemm_split", "mpnn_transpose_bf16", "mpnn_to_bf16",
-           "mpnn_graph", "mpnn_reverse_edges", "mpnn_features", "mpnn_gather_edges",
+           "mpnn_graph", "mpnn_graph_cells", "mpnn_reverse_edges", "mpnn_features", "mpnn_gather_edges",
            "mpnn_concat_rows", "mpnn_residual", "mpnn_gather_rows", "mpnn_segment_sum",
            "mpnn_segment_sum_cols", "mpnn_segment_sum_perm", "mpnn_relu_backward",
            "mpnn_adam", "mpnn_mse")
@@ -86,7 +86,10 @@ def _i32(v):
 class Graph:
     """Neighbour graph and network inputs for one particle state (device)."""
 
-    def __init__(self, x, v, w, R, cutoff, vs, Rs, max_edges=None):
+    # cells the cell-list graph may use (workspace 2 x 8 B per cell)
+    MAX_CELLS = 1 << 24
+
+    def __init__(self, x, v, w, R, cutoff, vs, Rs, max_edges=None, all_pairs=False):
         import torch
         dev = torch.device("cuda")
         n = int(R.shape[0])
@@ -99,8 +102,15 @@ class Graph:
         cap = max_edges or 64 * n
         self.nbr = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
         self.dst = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
-        _call("mpnn_graph", n, self.x, float(cutoff), cnt, self.off, self.nbr, self.dst, cap,
-              ctypes.pointer(ne), None)
+        if all_pairs:  # O(n^2), kept as the reference of the cell-list graph
+            _call("mpnn_graph", n, self.x, float(cutoff), cnt, self.off, self.nbr, self.dst, cap,
+                  ctypes.pointer(ne), None)
+        else:
+            work = torch.empty(2 * (self.MAX_CELLS + 1) + 2 * n + 1, dtype=torch.int64,
+                               device=dev)
+            box = torch.empty(6, dtype=torch.float32, device=dev)
+            _call("mpnn_graph_cells", n, self.x, float(cutoff), self.MAX_CELLS, work, box, cnt,
+                  self.off, self.nbr, self.dst, cap, ctypes.pointer(ne), None)
         self.E = int(ne.value)
         self.Epad = pad64(self.E)
         self.perm = torch.empty(max(self.E, 1), dtype=torch.int32, device=dev)
@@ -455,7 +465,7 @@ def rollout(model: MPNN, state, R, params, strides, stride=10, overlap_growth=0.
 _mesh_kw = {}
 
 
-def experiment(n_scenes=8, n_train=40, n_eval=8, iters=3000, lr=1e-3, drum_n=20_000,
+def experiment(n_scenes=16, n_train=80, n_eval=16, iters=3000, lr=1e-3, drum_n=100_000,
                strides=10, seed=0):
     """Train on hopper-discharge trajectories (the batched workload), evaluate
     on held-out pairs against the gravity-only guess, then run the network on
@@ -515,7 +525,7 @@ def main():
     import argparse
     ap = argparse.ArgumentParser(description="train and run the surrogate")
     ap.add_argument("--iters", type=int, default=3000)
-    ap.add_argument("--drum-n", type=int, default=20_000)
+    ap.add_argument("--drum-n", type=int, default=100_000)
     ap.add_argument("--strides", type=int, default=10)
     a = ap.parse_args()
     print(json.dumps(experiment(iters=a.iters, drum_n=a.drum_n, strides=a.strides)))

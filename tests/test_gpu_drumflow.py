@@ -1,9 +1,10 @@
 """The rotating drum's developed flow in both precisions (the drum workload's
-statistical comparison: free-surface angle and kinetic energy).  A 20,000-
-sphere drum turns one revolution; the last 60 % is sampled every 10 ms.  The
-precisions are compared statistically, not trajectory by trajectory (the
-flow is chaotic); at 100,000 spheres over 1.25 revolutions they agree within
-0.2 % on the angle and 0.1 % on the energies (drumflow.run, two seeds)."""
+statistical comparison: free-surface angle and kinetic energy), held to the
+1 % agreement the target states.  The precisions are compared statistically,
+not trajectory by trajectory (the flow is chaotic): the means over two seeds
+of 20,000-sphere drums.  At 100,000 spheres over 1.25 revolutions they agree
+within 0.2 % on the angle and 0.1 % on the energies (drumflow.run)."""
+import numpy as np
 import pytest
 
 pytestmark = pytest.mark.gpu
@@ -21,13 +22,22 @@ def drumflow():
 
 
 def test_developed_flow_agrees_between_precisions(drumflow):
-    out = {p: drumflow.run(n=20_000, precision=p, seed=5, revolutions=1.0, sample_from=0.4)
-           for p in (0, 1)}
-    for r in out.values():
-        assert r["status"] == 0 and r["samples"] >= 100
-        # a cascading bed: a steady inclined surface
-        assert 25.0 < r["angle_mean"] < 45.0 and r["angle_std"] < 3.0
-    a0, a1 = out[0]["angle_mean"], out[1]["angle_mean"]
-    assert abs(a0 - a1) < 0.03 * a0
-    for key in ("ke_trans_mean", "ke_rot_mean"):
-        assert abs(out[0][key] - out[1][key]) < 0.05 * out[0][key], key
+    # two seeds per precision, 1.2 revolutions, sampled every 10 ms over the
+    # last 70 %: the two-seed means agree within 1 % on the free-surface angle
+    # and the translational and rotational kinetic energy
+    seeds = (5, 6)
+    out = {p: [drumflow.run(n=20_000, precision=p, seed=sd, revolutions=1.2, sample_from=0.3)
+               for sd in seeds] for p in (0, 1)}
+    for runs in out.values():
+        for r in runs:
+            assert r["status"] == 0 and r["samples"] >= 150
+            # a cascading bed: a steady inclined surface
+            assert 25.0 < r["angle_mean"] < 45.0 and r["angle_std"] < 3.0
+    mean = {p: {key: float(np.mean([r[key] for r in runs]))
+                for key in ("angle_mean", "ke_trans_mean", "ke_rot_mean")}
+            for p, runs in out.items()}
+    print("drum flow, two-seed means (FP64, mixed):", mean[0], mean[1],
+          "per seed:", {p: [(r["angle_mean"], r["ke_trans_mean"], r["ke_rot_mean"]) for r in runs]
+                        for p, runs in out.items()})
+    for key in ("angle_mean", "ke_trans_mean", "ke_rot_mean"):
+        assert abs(mean[0][key] - mean[1][key]) < 0.01 * mean[0][key], key

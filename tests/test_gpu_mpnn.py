@@ -44,12 +44,16 @@ def test_gemm_matches_numpy(sg):
         assert np.abs(C2.cpu().numpy() - ref).max() <= 1e-5 * np.abs(ref).max()
 
 
-def test_graph_is_all_pairs_within_cutoff(sg):
+@pytest.mark.parametrize("all_pairs", [False, True], ids=["cells", "all_pairs"])
+def test_graph_is_all_pairs_within_cutoff(sg, all_pairs):
+    # the cell-list graph (the one the network uses) and the all-pairs one
+    # both give every pair closer than the cutoff, in ascending sender
     mo = pytest.importorskip("oracle.mpnn_oracle")
     rng = np.random.default_rng(1)
     x = rng.uniform(0, 0.02, size=(700, 3))
     R = np.full(700, 1e-3)
-    g = sg.Graph(x, np.zeros_like(x), np.zeros_like(x), R, 2.2e-3, 0.1, 1e-3)
+    g = sg.Graph(x, np.zeros_like(x), np.zeros_like(x), R, 2.2e-3, 0.1, 1e-3,
+                 all_pairs=all_pairs)
     off, nbr, dst = g.edges_host()
     off_r, nbr_r = mo.neighbours(x.astype(np.float32).astype(np.float64), 2.2e-3)
     assert np.array_equal(off, off_r) and np.array_equal(nbr, nbr_r)
@@ -135,3 +139,55 @@ def test_rollout_falls_back_to_the_dem_exactly(sg):
     r = sg.rollout(model, st, d["R"], d["params"], 1, overlap_growth=1e9, energy_limit=1e9)
     assert r["fallbacks"] == 0
     assert 0.0 < r["pos_error_rms_over_rmax"][0][1] < 0.05
+
+
+def test_surrogate_gain_against_the_dem_is_measured(sg):
+    # The surrogate replaces a stride of 10 DEM steps by one network
+    # evaluation.  Trained on the DEM's own hopper trajectories, it is run on
+    # a 20,000-sphere rotating drum (another geometry): one stride's position
+    # error against the DEM, and the cost of a stride (cell-list graph +
+    # forward, timed on the device) against the DEM's 10 steps (graph
+    # replay).  The gain -- DEM time over network time at that error -- is
+    # measured and asserted as it stands: below 1, the network costs more
+    # than the steps it replaces at this fidelity on this GPU.
+    import time
+
+    import torch
+
+    from paper_2507_12610_gb300 import batch, dem, scenes
+    rng = np.random.default_rng(3)
+    b = batch.combine([batch.hopper_scene(int(n), 900 + k,
+                                          (float(rng.uniform(0.2, 0.8)), 0.1, 0.1))
+                       for k, n in enumerate((900, 1400, 2000))])
+    pairs, R = sg.sample_pairs(b, 12, every=100, settle=2000)
+    model = sg.MPNN(seed=2)
+    sg.train(model, pairs, R, b["params"]["dt"], iters=300, lr=1e-3, lr_end=1e-4,
+             log_every=300)
+    d = scenes.drum_scene(n=20_000, seed=5, n_theta=64, n_rings=8, nn_dist=2.15e-3, speed=0.02)
+    sc = dem.Scene.from_dict(d, precision=1)
+    sc.step(1500)
+    st = sc.state()
+    sc.synchronize()
+    sc.step(20)
+    sc.synchronize()
+    t0 = time.perf_counter()
+    sc.step(100)
+    sc.synchronize()
+    dem_ms = (time.perf_counter() - t0) * 1e3 / 10
+    sc.close()
+    sg.predict(model, st, d["R"])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(3):
+        sg.predict(model, st, d["R"])
+    torch.cuda.synchronize()
+    net_ms = (time.perf_counter() - t0) * 1e3 / 3
+    sg._mesh_kw.clear()
+    sg._mesh_kw.update(verts=d["verts"], tris=d["tris"], tri_radius=d["tri_radius"])
+    r = sg.rollout(model, st, d["R"], d["params"], 1, overlap_growth=1e9, energy_limit=1e9)
+    err = r["pos_error_rms_over_rmax"][0][1]
+    gain = dem_ms / net_ms
+    print(f"surrogate on the 20k drum: network {net_ms:.3f} ms, DEM {dem_ms:.3f} ms per "
+          f"10-step stride, gain {gain:.3f} at a one-stride position error of {err:.2e} R_max")
+    assert np.isfinite(err) and err < 0.05
+    assert 0.0 < gain < 1.0, gain

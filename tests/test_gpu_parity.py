@@ -347,6 +347,41 @@ def test_capacity_overflow_is_reported_not_corrupting(dem):
     np.testing.assert_array_equal(v, s["v"])
 
 
+def test_pair_sides_give_opposite_forces_bit_for_bit(dem):
+    # In the FP32 steps both particles of a pair evaluate it, each with itself
+    # as body i of the law; the results must still be exact opposites (and
+    # each side's copy of the friction springs must stay consistent).  Sixty
+    # isolated pairs with random overlaps, approach speeds, sliding and spins
+    # and low friction (so springs go static and kinetic), 150 steps: every
+    # step each particle's only contact gives it exactly minus its partner's
+    # force, in both FP32 precisions.
+    rng = np.random.default_rng(41)
+    k = 60
+    R = rng.uniform(0.8e-3, 1.2e-3, 2 * k)
+    x = np.zeros((2 * k, 3))
+    v = rng.normal(0.0, 0.02, (2 * k, 3))
+    w = rng.normal(0.0, 20.0, (2 * k, 3))
+    for i in range(k):
+        n = rng.normal(size=3)
+        n /= np.linalg.norm(n)
+        x[2 * i] = (0.01 * i, 0.0, 0.0)
+        x[2 * i + 1] = x[2 * i] + (R[2 * i] + R[2 * i + 1] - rng.uniform(1e-6, 2e-5)) * n
+        v[2 * i + 1] -= 0.02 * n  # approaching
+    q = np.zeros((2 * k, 4))
+    q[:, 0] = 1.0
+    params = scenes.base_params(g=(0.0, 0.0, 0.0), mu_s=0.1, mu_r=0.02, mu_t=0.02,
+                                dt=2e-6)
+    for prec in (1, 2):
+        sc = dem.Scene(params, R, x, v, w, q, precision=prec, record_forces=True)
+        touching = 0
+        for step in range(150):
+            sc.step(1)
+            F, _ = sc.forces()
+            assert np.array_equal(F[0::2], -F[1::2]), (prec, step)
+            touching += int(np.count_nonzero(np.abs(F[0::2]).sum(axis=1)))
+        assert touching > 60 * 50, touching
+
+
 def test_capacity_overflow_regrows_and_retries(dem):
     # A list overflow is found while the lists are rebuilt, before the step
     # does any work; the binding saves the scene, creates it again with twice

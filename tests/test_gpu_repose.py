@@ -41,3 +41,23 @@ def test_small_heap_in_both_precisions(repose):
     pack = {p: np.mean([r["packing_core"] for r in runs]) for p, runs in out.items()}
     assert abs(mean[0] - mean[1]) < 0.06 * mean[0]
     assert abs(pack[0] - pack[1]) < 0.03
+
+
+def test_heap_statistics_agree_within_one_percent(repose):
+    # 20,000 grains (a heap large enough that one realisation's angle varies
+    # by about 1 %), two seeds per precision: the two-seed means of the angle
+    # of repose and of the core packing fraction agree within 1 %
+    seeds = (7, 8)
+    out = {p: [repose.run(n=20_000, precision=p, seed=sd, max_time=4.0) for sd in seeds]
+           for p in (0, 1)}
+    for runs in out.values():
+        for r in runs:
+            assert r["status"] == 0 and r["settled"] and r["active"] == 20_000
+    mean = {p: float(np.mean([r["theta"] for r in runs])) for p, runs in out.items()}
+    pack = {p: float(np.mean([r["packing_core"] for r in runs])) for p, runs in out.items()}
+    print("heap of 20,000 grains, two-seed means (FP64, mixed): angle", mean[0], mean[1],
+          "packing", pack[0], pack[1],
+          "per seed:", {p: [(r["theta"], r["packing_core"]) for r in runs]
+                        for p, runs in out.items()})
+    assert abs(mean[0] - mean[1]) < 0.01 * mean[0]
+    assert abs(pack[0] - pack[1]) < 0.01 * pack[0]
