@@ -928,6 +928,7 @@ int dem_scene_create(const dem_params* params, const dem_particles* parts, const
   s->bb.block_sums = M.get<uint32_t>(scan_block_sums_size(std::max<int64_t>(ncells + 1, n)) + 1);
   s->bb.tmp_nbr = M.get<uint32_t>((size_t)p.cap * n);
   s->bb.tmp_gid = M.get<uint32_t>((size_t)p.cap * n);
+  s->bb.tmp_hsrc = M.get<uint32_t>((size_t)p.cap * n);
   s->bb.tmp_cnt = M.get<uint32_t>(n);
   s->bb.tmp_offs = M.get<uint32_t>(n + 1);
   if (p.record_forces) s->forces = M.get<double>(6 * (size_t)n);

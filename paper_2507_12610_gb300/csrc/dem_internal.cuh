@@ -184,6 +184,8 @@ struct MeshDev {
   int32_t nv, nt;
 };
 
+constexpr uint32_t kNoHist = 0xffffffffu;  // no history record to carry over
+
 // Binning scratch.
 struct BinBuf {
   uint32_t* key;        // [n] cell of each slot (current order)
@@ -194,6 +196,8 @@ struct BinBuf {
   uint32_t* block_sums; // scan partials
   uint32_t* tmp_nbr;    // [cap][n] candidates of the list being built (slot order)
   uint32_t* tmp_gid;    // [cap][n] their caller indices
+  uint32_t* tmp_hsrc;   // [cap][n] index of the entry's history record in the
+                        //   previous list, or kNoHist
   uint32_t* tmp_cnt;    // [n] their counts
   uint32_t* tmp_offs;   // [n + 1] exclusive prefix of the counts
   // triangle cell lists

@@ -259,67 +259,29 @@ k_tri_cell_sort(const Ctl* ctl, Params p, BinBuf bb) {
 // contact's history over from the particle's previous list.  The pair list is
 // packed into CSR form by k_list_compact once the counts are scanned.
 //
-// Shared-memory staging of the neighbour cells: slots are in cell order, so a
-// block of consecutive slots lies in one or two rows of cells (fixed y, z);
-// for each such row the block loads the positions and caller indices of the
-// particles in its nine neighbour rows (over the x range the block's
-// particles reach) into shared memory once, and every thread then tests its
-// candidates from there.  A block whose particles span more rows, or whose
-// neighbourhood does not fit, reads its candidates from global memory; the
-// lists are the same either way.
+// One thread per slot; the candidate positions come through L1 (a block's
+// slots are neighbours in cell order, so they read the same cells).  Staging
+// the neighbour rows of a block in shared memory first was measured slower
+// (the threads of a block that spans two rows of cells wait for each other).
 constexpr int kBuildThreads = 128;
-constexpr int kStageCap = 1536;  // staged particles per block and row group
 
 template <typename Hist>
 __global__ void __launch_bounds__(kBuildThreads)
 k_list_build(Ctl* ctl, Params p, BinBuf bb, Lists L, MeshDev mesh) {
-  __shared__ float4 s_pos[kStageCap];
-  __shared__ uint32_t s_gid[kStageCap];
-  __shared__ uint32_t s_a[9], s_off[10];
-  __shared__ int s_row[2], s_xlo[2], s_xhi[2];
-  if (!rebuilding(ctl)) return;  // the same for every thread of the block
+  if (!rebuilding(ctl)) return;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int n = p.n;
+  if (t >= n) return;
   const ListBuf lo = list_of(L, ctl->lphase & 1u);
   const ListBuf ln = list_of(L, (ctl->lphase & 1u) ^ 1u);
-  bool active = false;
-  float4 X = make_float4(0.f, 0.f, 0.f, 0.f);
-  int3 c = make_int3(0, 0, 0);
-  int row = -1;
-  if (t < n) {
-    X = ln.posf[t];
-    active = X.w != 0.f;
-    if (!active) {  // inactive: no list, no mesh candidates
-      bb.tmp_cnt[t] = 0u;
-      ln.meta[t] = 0u;
-    } else {
-      c = cell_coords(p, X.x, X.y, X.z);
-      row = c.z * p.nc[1] + c.y;
-    }
+  const float4 X = ln.posf[t];
+  if (X.w == 0.f) {  // inactive: no list, no mesh candidates
+    bb.tmp_cnt[t] = 0u;
+    ln.meta[t] = 0u;
+    return;
   }
-  if (threadIdx.x == 0) {
-    s_row[0] = 0x7fffffff;
-    s_row[1] = -1;
-    s_xlo[0] = s_xlo[1] = 0x7fffffff;
-    s_xhi[0] = s_xhi[1] = -1;
-  }
-  __syncthreads();
-  if (active) {
-    atomicMin(&s_row[0], row);
-    atomicMax(&s_row[1], row);
-  }
-  __syncthreads();
-  const int r0 = s_row[0], r1 = s_row[1];
-  const int staged_ok = __syncthreads_and(!active || row == r0 || row == r1);
-  const int grp = active ? (row == r0 ? 0 : 1) : -1;
-  if (active && staged_ok) {
-    atomicMin(&s_xlo[grp], c.x);
-    atomicMax(&s_xhi[grp], c.x);
-  }
-  __syncthreads();
-  const int ngroups = r1 < 0 ? 0 : (r0 == r1 ? 1 : 2);
-
-  const uint32_t gt = active ? ln.gid[t] : 0u;
+  const int3 c = cell_coords(p, X.x, X.y, X.z);
+  const uint32_t gt = ln.gid[t];
   uint32_t cand_g[64];
   uint32_t cand_s[64];
   const int cap = min(p.cap, 64);
@@ -328,105 +290,70 @@ k_list_build(Ctl* ctl, Params p, BinBuf bb, Lists L, MeshDev mesh) {
   // the cells of a row along x are consecutive in the grid, so the three
   // cells x-1 .. x+1 of a neighbour row are one range of slots: 9 ranges
   const int x0 = max(c.x - 1, 0), x1 = min(c.x + 1, p.nc[0] - 1);
-  auto scan = [&](bool staged) {
-    for (int dz = -1; dz <= 1; ++dz) {
-      const int cz = c.z + dz;
-      if (cz < 0 || cz >= p.nc[2]) continue;
-      for (int dy = -1; dy <= 1; ++dy) {
-        const int cy = c.y + dy;
-        if (cy < 0 || cy >= p.nc[1]) continue;
-        const int r = (dz + 1) * 3 + (dy + 1);
-        const uint32_t a = bb.cell_start[cell_index(p, make_int3(x0, cy, cz))];
-        const uint32_t b = bb.cell_start[cell_index(p, make_int3(x1, cy, cz)) + 1];
-        for (uint32_t u = a; u < b; ++u) {
-          if (u == (uint32_t)t) continue;
-          float4 Y;
-          uint32_t gu = 0;
-          if (staged) {
-            const uint32_t k = s_off[r] + (u - s_a[r]);
-            Y = s_pos[k];
-            gu = s_gid[k];
-          } else {
-            Y = ln.posf[u];
-          }
-          const float ddx = X.x - Y.x, ddy = X.y - Y.y, ddz = X.z - Y.z;
-          const float cut = X.w + Y.w + p.skin + p.list_margin;
-          if (ddx * ddx + ddy * ddy + ddz * ddz < cut * cut) {
-            if (cnt < cap) {
-              const uint32_t g = staged ? gu : ln.gid[u];
-              int j = cnt;
-              while (j > 0 && cand_g[j - 1] > g) {
-                cand_g[j] = cand_g[j - 1];
-                cand_s[j] = cand_s[j - 1];
-                --j;
-              }
-              cand_g[j] = g;
-              cand_s[j] = u;
-              ++cnt;
-            } else {
-              overflow = true;
+  for (int dz = -1; dz <= 1; ++dz) {
+    const int cz = c.z + dz;
+    if (cz < 0 || cz >= p.nc[2]) continue;
+    for (int dy = -1; dy <= 1; ++dy) {
+      const int cy = c.y + dy;
+      if (cy < 0 || cy >= p.nc[1]) continue;
+      const uint32_t a = bb.cell_start[cell_index(p, make_int3(x0, cy, cz))];
+      const uint32_t b = bb.cell_start[cell_index(p, make_int3(x1, cy, cz)) + 1];
+      for (uint32_t u = a; u < b; ++u) {
+        if (u == (uint32_t)t) continue;
+        const float4 Y = ln.posf[u];
+        const float ddx = X.x - Y.x, ddy = X.y - Y.y, ddz = X.z - Y.z;
+        const float cut = X.w + Y.w + p.skin + p.list_margin;
+        if (ddx * ddx + ddy * ddy + ddz * ddz < cut * cut) {
+          if (cnt < cap) {
+            const uint32_t g = ln.gid[u];
+            int j = cnt;
+            while (j > 0 && cand_g[j - 1] > g) {
+              cand_g[j] = cand_g[j - 1];
+              cand_s[j] = cand_s[j - 1];
+              --j;
             }
+            cand_g[j] = g;
+            cand_s[j] = u;
+            ++cnt;
+          } else {
+            overflow = true;
           }
         }
       }
-    }
-  };
-  if (!staged_ok) {
-    if (active) scan(false);
-  } else {
-    for (int gi = 0; gi < ngroups; ++gi) {
-      // the nine neighbour rows of row group gi over the x range its
-      // particles reach, one after another in shared memory
-      if (threadIdx.x == 0) {
-        const int rr = gi == 0 ? r0 : r1;
-        const int cy0 = rr % p.nc[1], cz0 = rr / p.nc[1];
-        const int xa = max(s_xlo[gi] - 1, 0), xb = min(s_xhi[gi] + 1, p.nc[0] - 1);
-        uint32_t tot = 0;
-        for (int r = 0; r < 9; ++r) {
-          const int cz = cz0 + r / 3 - 1, cy = cy0 + r % 3 - 1;
-          uint32_t a = 0, b = 0;
-          if (cz >= 0 && cz < p.nc[2] && cy >= 0 && cy < p.nc[1]) {
-            a = bb.cell_start[cell_index(p, make_int3(xa, cy, cz))];
-            b = bb.cell_start[cell_index(p, make_int3(xb, cy, cz)) + 1];
-          }
-          s_a[r] = a;
-          s_off[r] = tot;
-          tot += b - a;
-        }
-        s_off[9] = tot;
-      }
-      __syncthreads();
-      const uint32_t tot = s_off[9];
-      const bool fits = tot <= (uint32_t)kStageCap;
-      if (fits) {
-        for (uint32_t k = threadIdx.x; k < tot; k += blockDim.x) {
-          int r = 0;
-          while (r < 8 && s_off[r + 1] <= k) ++r;
-          const uint32_t u = s_a[r] + (k - s_off[r]);
-          s_pos[k] = ln.posf[u];
-          s_gid[k] = ln.gid[u];
-        }
-      }
-      __syncthreads();
-      if (active && grp == gi) scan(fits);
-      __syncthreads();
     }
   }
-  if (!active) return;
   if (overflow) set_status(ctl, DEM_ERR_CAPACITY);
   int nlow = 0;
+  while (nlow < cnt && cand_g[nlow] < gt) ++nlow;
+  // the pair history to carry over: both this list and the particle's
+  // previous one are sorted by partner caller index, so one merge walk finds
+  // each partner's old entry; a record counts only if the contact touched in
+  // the previous step (with one evaluation per pair only the entries of
+  // partners with a higher caller index hold records)
+  const uint32_t s = bb.order[t];
+  const uint32_t mo = lo.meta[s];
+  const int nn_o = (int)(mo & 0xffu);
+  const uint32_t off_o = lo.offs[s];
+  const Hist* hpp_o = static_cast<const Hist*>(lo.hpp);
+  const uint32_t stamp_now = (uint32_t)ctl->step;  // records written in the previous step
+  const int khist = p.pair_res ? nlow : 0;
+  int io = 0;
   for (int k = 0; k < cnt; ++k) {
-    if (cand_g[k] < gt) ++nlow;
+    const uint32_t g = cand_g[k];
+    uint32_t src = kNoHist;
+    if (k >= khist) {
+      while (io < nn_o && lo.ngid[off_o + io] < g) ++io;
+      if (io < nn_o && lo.ngid[off_o + io] == g && hpp_o[off_o + io].stamp == stamp_now)
+        src = off_o + (uint32_t)io;
+    }
     bb.tmp_nbr[(size_t)k * n + t] = cand_s[k];
-    bb.tmp_gid[(size_t)k * n + t] = cand_g[k];
+    bb.tmp_gid[(size_t)k * n + t] = g;
+    bb.tmp_hsrc[(size_t)k * n + t] = src;
   }
   bb.tmp_cnt[t] = (uint32_t)cnt;
 
   // triangle candidates (fixed capacity per particle), history carried over
-  const uint32_t s = bb.order[t];
-  const uint32_t mo = lo.meta[s];
   const int nt_o = (int)((mo >> 16) & 0xffu);
-  const uint32_t stamp_now = (uint32_t)ctl->step;  // records written in the previous step
   int ntc = 0;
   if (mesh.nt > 0) {
     const uint32_t cell = cell_index(p, c);
@@ -466,12 +393,10 @@ k_list_build(Ctl* ctl, Params p, BinBuf bb, Lists L, MeshDev mesh) {
 }
 
 // Pack the new pair lists into CSR form (offsets from the scan of the counts)
-// and carry each pair's friction history over from the particle's previous
-// list (kept only if the contact touched in the previous step).  A warp
-// covers the entries of 32 consecutive slots, 32 entries at a time (all lanes
-// busy, consecutive entries written by consecutive lanes); each entry finds
-// its old record by a binary search of its partner's caller index in the
-// particle's previous list, which is sorted by it.
+// and copy each pair's friction history record from the previous list where
+// k_list_build found one.  A warp covers the entries of 32 consecutive slots,
+// 32 entries at a time (all lanes busy, consecutive entries written by
+// consecutive lanes).
 constexpr int kCompactWarps = 4;
 
 __device__ __forceinline__ uint32_t warp_scan_incl(uint32_t v) {
@@ -498,16 +423,9 @@ k_list_compact(Ctl* ctl, Params p, BinBuf bb, Lists L) {
   const ListBuf lo = list_of(L, ctl->lphase & 1u);
   const ListBuf ln = list_of(L, (ctl->lphase & 1u) ^ 1u);
   uint32_t* seg = seg_s[wib];
-  uint32_t cnt = 0, off_o = 0, nn_o = 0, k0 = 0;
+  uint32_t cnt = 0;
   if (t <= n) ln.offs[t] = bb.tmp_offs[t];
-  if (t < n) {
-    cnt = bb.tmp_cnt[t];
-    const uint32_t s = bb.order[t];
-    off_o = lo.offs[s];
-    nn_o = lo.meta[s] & 0xffu;
-    // with one evaluation per pair only the upper entries carry history
-    k0 = p.pair_res ? (ln.meta[t] >> 8) & 0xffu : 0u;
-  }
+  if (t < n) cnt = bb.tmp_cnt[t];
   const uint32_t incl = warp_scan_incl(cnt);
   seg[lane + 1] = incl;
   if (lane == 0) seg[0] = 0;
@@ -516,36 +434,20 @@ k_list_compact(Ctl* ctl, Params p, BinBuf bb, Lists L) {
   __syncwarp();
   const Hist* hpp_o = static_cast<const Hist*>(lo.hpp);
   Hist* hpp_n = static_cast<Hist*>(ln.hpp);
-  const uint32_t stamp_now = (uint32_t)ctl->step;
   for (uint32_t e0 = 0; e0 < E; e0 += 32) {
     const uint32_t e = e0 + lane;
+    if (e >= E) break;
+    // the slot owning entry e: largest tl with seg[tl] <= e
     int tl = 0;
-    if (e < E) {
-      // the slot owning entry e: largest tl with seg[tl] <= e
 #pragma unroll
-      for (int step = 16; step > 0; step >>= 1)
-        if (seg[tl + step] <= e) tl += step;
-    }
-    const uint32_t o_off = __shfl_sync(full, off_o, tl);
-    const uint32_t o_nn = __shfl_sync(full, nn_o, tl);
-    const uint32_t o_k0 = __shfl_sync(full, k0, tl);
-    if (e >= E) continue;
+    for (int step = 16; step > 0; step >>= 1)
+      if (seg[tl + step] <= e) tl += step;
     const uint32_t k = e - seg[tl];
     const size_t src = (size_t)k * n + (size_t)(w0 + tl);
-    const uint32_t u = bb.tmp_nbr[src], g = bb.tmp_gid[src];
-    ln.nbr[base + e] = u;
-    ln.ngid[base + e] = g;
-    if (k < o_k0 || o_nn == 0u) continue;
-    uint32_t a = 0, b = o_nn;
-    while (a < b) {
-      const uint32_t mid = (a + b) >> 1;
-      if (lo.ngid[o_off + mid] < g) a = mid + 1;
-      else b = mid;
-    }
-    if (a < o_nn && lo.ngid[o_off + a] == g) {
-      const Hist h = hpp_o[o_off + a];
-      if (h.stamp == stamp_now) hpp_n[base + e] = h;
-    }
+    ln.nbr[base + e] = bb.tmp_nbr[src];
+    ln.ngid[base + e] = bb.tmp_gid[src];
+    const uint32_t hs = bb.tmp_hsrc[src];
+    if (hs != kNoHist) hpp_n[base + e] = hpp_o[hs];
   }
 }
 

@@ -74,6 +74,23 @@ def run(n=20_000, precision=1, seed=7, max_time=20.0, check=0.02, rest_speed=2e-
     }
 
 
+def run_many(jobs, workers=None) -> list:
+    """Run several heaps at once (a list of keyword dicts for run()), each on a
+    CUDA stream of its own from a host thread of its own, so that small heaps
+    share the GPU; results in the order of the jobs.  Each heap computes
+    exactly what it computes alone."""
+    import concurrent.futures as cf
+
+    import torch
+
+    def one(kw):
+        with torch.cuda.stream(torch.cuda.Stream()):
+            return run(**kw)
+
+    with cf.ThreadPoolExecutor(max_workers=workers or len(jobs)) as ex:
+        return list(ex.map(one, jobs))
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--n", type=int, default=20_000)

@@ -44,20 +44,23 @@ def test_small_heap_in_both_precisions(repose):
 
 
 def test_heap_statistics_agree_within_one_percent(repose):
-    # 20,000 grains (a heap large enough that one realisation's angle varies
-    # by about 1 %), two seeds per precision: the two-seed means of the angle
-    # of repose and of the core packing fraction agree within 1 %
-    seeds = (7, 8)
-    out = {p: [repose.run(n=20_000, precision=p, seed=sd, max_time=4.0) for sd in seeds]
-           for p in (0, 1)}
+    # 20,000 grains.  One realisation's angle scatters by about 0.45 degrees
+    # (1.1 %) from seed to seed, so the precisions are compared on the means
+    # of six seeds each (standard error about 0.2 degrees); the twelve heaps
+    # run at once, each on its own stream, and each computes what it computes
+    # alone (the runs are deterministic)
+    seeds = (7, 8, 9, 10, 11, 12)
+    jobs = [dict(n=20_000, precision=p, seed=sd, max_time=4.0) for p in (0, 1) for sd in seeds]
+    res = repose.run_many(jobs)
+    out = {0: res[:len(seeds)], 1: res[len(seeds):]}
     for runs in out.values():
         for r in runs:
             assert r["status"] == 0 and r["settled"] and r["active"] == 20_000
     mean = {p: float(np.mean([r["theta"] for r in runs])) for p, runs in out.items()}
     pack = {p: float(np.mean([r["packing_core"] for r in runs])) for p, runs in out.items()}
-    print("heap of 20,000 grains, two-seed means (FP64, mixed): angle", mean[0], mean[1],
+    print("heap of 20,000 grains, six-seed means (FP64, mixed): angle", mean[0], mean[1],
           "packing", pack[0], pack[1],
-          "per seed:", {p: [(r["theta"], r["packing_core"]) for r in runs]
+          "per seed:", {p: [(r["seed"], r["theta"], r["packing_core"]) for r in runs]
                         for p, runs in out.items()})
     assert abs(mean[0] - mean[1]) < 0.01 * mean[0]
     assert abs(pack[0] - pack[1]) < 0.01 * pack[0]
