@@ -327,14 +327,13 @@ k_list_build(Ctl* ctl, Params p, BinBuf bb, Lists L, MeshDev mesh) {
   while (nlow < cnt && cand_g[nlow] < gt) ++nlow;
   // the pair history to carry over: both this list and the particle's
   // previous one are sorted by partner caller index, so one merge walk finds
-  // each partner's old entry; a record counts only if the contact touched in
-  // the previous step (with one evaluation per pair only the entries of
-  // partners with a higher caller index hold records)
+  // each partner's old entry (with one evaluation per pair only the entries
+  // of partners with a higher caller index hold records); k_list_compact
+  // keeps the record only if the contact touched in the previous step
   const uint32_t s = bb.order[t];
   const uint32_t mo = lo.meta[s];
   const int nn_o = (int)(mo & 0xffu);
   const uint32_t off_o = lo.offs[s];
-  const Hist* hpp_o = static_cast<const Hist*>(lo.hpp);
   const uint32_t stamp_now = (uint32_t)ctl->step;  // records written in the previous step
   const int khist = p.pair_res ? nlow : 0;
   int io = 0;
@@ -343,8 +342,7 @@ k_list_build(Ctl* ctl, Params p, BinBuf bb, Lists L, MeshDev mesh) {
     uint32_t src = kNoHist;
     if (k >= khist) {
       while (io < nn_o && lo.ngid[off_o + io] < g) ++io;
-      if (io < nn_o && lo.ngid[off_o + io] == g && hpp_o[off_o + io].stamp == stamp_now)
-        src = off_o + (uint32_t)io;
+      if (io < nn_o && lo.ngid[off_o + io] == g) src = off_o + (uint32_t)io;
     }
     bb.tmp_nbr[(size_t)k * n + t] = cand_s[k];
     bb.tmp_gid[(size_t)k * n + t] = g;
@@ -394,7 +392,7 @@ k_list_build(Ctl* ctl, Params p, BinBuf bb, Lists L, MeshDev mesh) {
 
 // Pack the new pair lists into CSR form (offsets from the scan of the counts)
 // and copy each pair's friction history record from the previous list where
-// k_list_build found one.  A warp covers the entries of 32 consecutive slots,
+// k_list_build found one and the contact touched in the previous step.  A warp covers the entries of 32 consecutive slots,
 // 32 entries at a time (all lanes busy, consecutive entries written by
 // consecutive lanes).
 constexpr int kCompactWarps = 4;
@@ -434,6 +432,7 @@ k_list_compact(Ctl* ctl, Params p, BinBuf bb, Lists L) {
   __syncwarp();
   const Hist* hpp_o = static_cast<const Hist*>(lo.hpp);
   Hist* hpp_n = static_cast<Hist*>(ln.hpp);
+  const uint32_t stamp_now = (uint32_t)ctl->step;  // records written in the previous step
   for (uint32_t e0 = 0; e0 < E; e0 += 32) {
     const uint32_t e = e0 + lane;
     if (e >= E) break;
@@ -447,7 +446,10 @@ k_list_compact(Ctl* ctl, Params p, BinBuf bb, Lists L) {
     ln.nbr[base + e] = bb.tmp_nbr[src];
     ln.ngid[base + e] = bb.tmp_gid[src];
     const uint32_t hs = bb.tmp_hsrc[src];
-    if (hs != kNoHist) hpp_n[base + e] = hpp_o[hs];
+    if (hs != kNoHist) {
+      const Hist h = hpp_o[hs];
+      if (h.stamp == stamp_now) hpp_n[base + e] = h;
+    }
   }
 }
 
