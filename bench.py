@@ -290,6 +290,15 @@ def kernel_sources_sha1() -> str:
     return h.hexdigest()
 
 
+def sphere_count(n: int) -> str:
+    """1000000 -> '1M', 400000 -> '400k'."""
+    if n % 1_000_000 == 0:
+        return f"{n // 1_000_000}M"
+    if n % 1000 == 0:
+        return f"{n // 1000}k"
+    return str(n)
+
+
 def measured_traffic(n: int, mixed: bool):
     """DRAM bytes per step-kernel launch from the committed ncu summary.
 
@@ -388,7 +397,7 @@ def bench_ours(a):
            "warmup": a.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None,
            "dtype": "f32" if prec == dem.DEM_MIXED else "f64", "data": "synthetic",
-           "config": {"workload": "rotating drum, 1M spheres R~U[0.8,1.2] mm, 4096-triangle "
+           "config": {"workload": f"rotating drum, {sphere_count(n)} spheres R~U[0.8,1.2] mm, 4096-triangle "
                                   "cylinder at 30 rpm, 35% fill, mu 0.4/0.05/0.05",
                       "n_particles": n, "n_triangles": int(s["tris"].shape[0]),
                       "precision": ("mixed: FP32 contact math, compensated double-float state"
