@@ -188,6 +188,26 @@ typedef struct dem_scene dem_scene;
 int dem_scene_create(const dem_params* params, const dem_particles* particles,
                      const dem_mesh* mesh, void* stream, dem_scene** out);
 
+/* Device memory supplied by the caller (for instance a framework's caching
+ * allocator).  alloc returns a block of `bytes` bytes of device memory on the
+ * current device, aligned to 256 bytes, or NULL; release returns a block
+ * obtained from alloc.  Both get the caller's `ctx`. */
+typedef void* (*dem_alloc_fn)(size_t bytes, void* ctx);
+typedef void (*dem_free_fn)(void* ptr, void* ctx);
+
+/* dem_scene_create with every device buffer of the scene taken from `alloc`
+ * (the library still creates its streams, events and graphs itself).  The
+ * blocks are returned through `release` when the scene is destroyed, after its
+ * stream has drained, or at once if creation fails; both functions must stay
+ * callable until then.  An allocator interface for the scene's memory
+ * (ownership stays with the scene; the paper has no counterpart).
+ * Errors: as dem_scene_create; DEM_ERR_INVALID if exactly one of alloc and
+ * release is NULL (both NULL: cudaMalloc, as dem_scene_create); DEM_ERR_NOMEM
+ * if alloc returns NULL or a block that is not 256-byte aligned. */
+int dem_scene_create_with_allocator(const dem_params* params, const dem_particles* particles,
+                                    const dem_mesh* mesh, void* stream, dem_alloc_fn alloc,
+                                    dem_free_fn release, void* ctx, dem_scene** out);
+
 /* Enqueue `nsteps` time steps on the scene's stream and return without
  * waiting.  Each step: mesh pose, rebuild check, (cell binning, Verlet list and
  * history remap when needed: Sec. 3.3 and the Verlet lists suggested in Sec.

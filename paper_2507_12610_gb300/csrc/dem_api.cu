@@ -18,14 +18,31 @@ namespace {
 
 constexpr int kGraphSteps = 16;  // steps per replay of the long graph
 
+// Device memory of a scene: cudaMalloc, or the caller's allocator
+// (dem_scene_create_with_allocator).  Every block is released with the scene.
 struct Alloc {
   std::vector<void*> ptrs;
   bool failed = false;
+  dem_alloc_fn user_alloc = nullptr;
+  dem_free_fn user_free = nullptr;
+  void* user_ctx = nullptr;
   template <typename T>
   T* get(size_t count) {
     void* p = nullptr;
+    if (failed) return nullptr;  // creation fails anyway; allocate nothing more
     if (count == 0) count = 1;
-    if (cudaMalloc(&p, count * sizeof(T)) != cudaSuccess) {
+    const size_t bytes = count * sizeof(T);
+    if (user_alloc) {
+      p = user_alloc(bytes, user_ctx);
+      if (p && (reinterpret_cast<uintptr_t>(p) & 255u) != 0) {  // records need alignment
+        user_free(p, user_ctx);
+        p = nullptr;
+      }
+      if (!p) {
+        failed = true;
+        return nullptr;
+      }
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
       failed = true;
       cudaGetLastError();
       return nullptr;
@@ -34,7 +51,12 @@ struct Alloc {
     return static_cast<T*>(p);
   }
   void release() {
-    for (void* p : ptrs) cudaFree(p);
+    for (void* p : ptrs) {
+      if (user_alloc)
+        user_free(p, user_ctx);
+      else
+        cudaFree(p);
+    }
     ptrs.clear();
   }
 };
@@ -667,8 +689,16 @@ const char* dem_status_string(int status) {
 
 int dem_scene_create(const dem_params* params, const dem_particles* parts, const dem_mesh* mesh,
                      void* stream, dem_scene** out) {
+  return dem_scene_create_with_allocator(params, parts, mesh, stream, nullptr, nullptr, nullptr,
+                                         out);
+}
+
+int dem_scene_create_with_allocator(const dem_params* params, const dem_particles* parts,
+                                    const dem_mesh* mesh, void* stream, dem_alloc_fn alloc,
+                                    dem_free_fn release, void* ctx, dem_scene** out) {
   if (!out) return DEM_ERR_INVALID;
   *out = nullptr;
+  if ((alloc == nullptr) != (release == nullptr)) return DEM_ERR_INVALID;
   int rc = validate(params, parts, mesh);
   if (rc != DEM_OK) return rc;
   ElemTable et;
@@ -676,6 +706,9 @@ int dem_scene_create(const dem_params* params, const dem_particles* parts, const
   if (rc != DEM_OK) return rc;
   dem_scene* s = new (std::nothrow) dem_scene();
   if (!s) return DEM_ERR_NOMEM;
+  s->mem.user_alloc = alloc;
+  s->mem.user_free = release;
+  s->mem.user_ctx = ctx;
   auto fail = [&](int code) {
     destroy(s);
     return code;

@@ -37,7 +37,12 @@ _DP = ctypes.POINTER(ctypes.c_double)
 EXPORTS = ("dem_scene_create", "dem_step", "dem_synchronize", "dem_read_state",
            "dem_read_forces", "dem_read_contacts", "dem_get_stats", "dem_save", "dem_load",
            "dem_scene_destroy", "dem_status_string", "dem_step_timed",
-           "dem_contact_forces_noalloc", "dem_read_radii", "dem_probe_fp64_fma")
+           "dem_contact_forces_noalloc", "dem_read_radii", "dem_probe_fp64_fma",
+           "dem_scene_create_with_allocator")
+
+# dem_alloc_fn / dem_free_fn
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 
 
 class dem_params(ctypes.Structure):
@@ -93,6 +98,9 @@ def load(path: str = LIB_PATH):
     P = ctypes.c_void_p
     lib.dem_scene_create.argtypes = [ctypes.POINTER(dem_params), ctypes.POINTER(dem_particles),
                                      ctypes.POINTER(dem_mesh), P, ctypes.POINTER(P)]
+    lib.dem_scene_create_with_allocator.argtypes = [
+        ctypes.POINTER(dem_params), ctypes.POINTER(dem_particles), ctypes.POINTER(dem_mesh), P,
+        ALLOC_FN, FREE_FN, P, ctypes.POINTER(P)]
     lib.dem_step.argtypes = [P, _I64]
     lib.dem_synchronize.argtypes = [P]
     lib.dem_step_timed.argtypes = [P, _I64, _DP]
@@ -202,6 +210,34 @@ def current_stream():
     return None
 
 
+class TorchAllocator:
+    """Device memory for scenes from PyTorch's caching allocator, handed to
+    dem_scene_create_with_allocator (the blocks count in
+    torch.cuda.memory_allocated and return to torch's pool when the scene is
+    destroyed).  `live` maps each block the library holds to its size."""
+
+    def __init__(self, device=None, stream=None):
+        import torch
+        self._torch = torch
+        self.device = torch.cuda.current_device() if device is None else device
+        self.stream = stream
+        self.live = {}
+        self.alloc_fn = ALLOC_FN(self._alloc)
+        self.free_fn = FREE_FN(self._free)
+
+    def _alloc(self, nbytes, ctx):
+        try:
+            p = self._torch.cuda.caching_allocator_alloc(int(nbytes), self.device, self.stream)
+        except RuntimeError:  # out of memory: the library reports DEM_ERR_NOMEM
+            return None
+        self.live[int(p)] = int(nbytes)
+        return p
+
+    def _free(self, ptr, ctx):
+        self.live.pop(int(ptr), None)
+        self._torch.cuda.caching_allocator_delete(ptr)
+
+
 class Scene:
     """Owner of one `dem_scene*` created from host arrays."""
 
@@ -210,7 +246,7 @@ class Scene:
                  precision: int = DEM_FP64, skin: float = 0.0,
                  max_neighbors: int = 0, max_mesh_contacts: int = 0,
                  record_forces: bool = False, domain=None, stream=None, spawn=None,
-                 material=None, material_mu=None, step_warps: int = 0):
+                 material=None, material_mu=None, step_warps: int = 0, allocator=None):
         lib = load()
         self._lib = lib
         self._h = ctypes.c_void_p()
@@ -219,7 +255,8 @@ class Scene:
         self._init_kw = dict(precision=precision, skin=skin, max_neighbors=max_neighbors,
                              max_mesh_contacts=max_mesh_contacts, record_forces=record_forces,
                              domain=domain, stream=stream, spawn=spawn, material=material,
-                             material_mu=material_mu, step_warps=step_warps)
+                             material_mu=material_mu, step_warps=step_warps,
+                             allocator=allocator)
         R = _f64(R, (-1,))
         n = R.shape[0]
         # rows: the given particles, then (with spawning) inactive rows up to n_max
@@ -262,8 +299,15 @@ class Scene:
             keep += [V, T, Rt, El, Re]
         self.n_tri = me.n_tri + me.n_elem  # mesh elements (triangles first)
         st = stream if stream is not None else current_stream()
-        rc = lib.dem_scene_create(ctypes.byref(self._pp), ctypes.byref(pa), ctypes.byref(me), st,
-                                  ctypes.byref(self._h))
+        # the allocator's callbacks must outlive the scene (they free its blocks)
+        self._allocator = allocator
+        if allocator is None:
+            rc = lib.dem_scene_create(ctypes.byref(self._pp), ctypes.byref(pa), ctypes.byref(me),
+                                      st, ctypes.byref(self._h))
+        else:
+            rc = lib.dem_scene_create_with_allocator(
+                ctypes.byref(self._pp), ctypes.byref(pa), ctypes.byref(me), st,
+                allocator.alloc_fn, allocator.free_fn, None, ctypes.byref(self._h))
         del keep
         _check(rc, "dem_scene_create")
 
