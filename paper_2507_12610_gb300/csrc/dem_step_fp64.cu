@@ -41,6 +41,12 @@ struct Fp64Policy {
       F = F + mk(c[0], c[1], c[2]);
       T = T + mk(c[3], c[4], c[5]);
     }
+    // one component at a time (plain sums: l is not used)
+    static __device__ __forceinline__ void add1(double& h, double&, double v) { h = h + v; }
+    __device__ __forceinline__ void set(const double* h, const double*) {
+      F = mk(h[0], h[1], h[2]);
+      T = mk(h[3], h[4], h[5]);
+    }
   };
 
   struct Geo {

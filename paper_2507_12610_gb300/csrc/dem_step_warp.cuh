@@ -10,8 +10,11 @@
 //      contiguous and in ascending partner index;
 //   B. the lanes evaluate the contact law for 32 queued contacts at a time
 //      (all lanes busy), write the friction history, and park each contact's
-//      force/torque on its own particle in shared memory; then every lane adds
-//      the parked contributions of its own particle in queue order;
+//      force/torque on its own particle in shared memory; then the parked
+//      contributions are added to the particles' sums in queue order, one
+//      lane per (particle, component) of the batch, the sums kept in shared
+//      memory (six independent sequences per particle, so the lanes share the
+//      work and every component is summed in the same order as by one lane);
 //      A and B alternate in rounds whenever the queue is full, which keeps
 //      the order and bounds the shared memory;
 //   M. the lanes evaluate the particle-element contacts of the warp's
@@ -42,6 +45,8 @@ struct WarpScratch {
   uint16_t qcode[kQueueMax];  // (particle << 6) | entry
   uint32_t qslot[kQueueMax];  // partner slot
   CT contrib[32][6];
+  CT acc_h[32][6];  // per-particle sums of phase B (hi words, or the sums)
+  CT acc_l[32][6];  // their compensation words (unused by plain sums)
 };
 
 __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
@@ -94,7 +99,11 @@ k_step_warp(Ctl* ctl, Params p, StateBufs sb, Lists L, MeshDev mesh, double* for
 
   uint32_t npair = 0;
   typename Pol::Acc acc;
-  acc.zero();
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    S.acc_h[lane][c] = CT(0);
+    S.acc_l[lane][c] = CT(0);
+  }
   uint32_t e0 = 0;
   do {
     S.cnt[lane] = 0;
@@ -133,7 +142,6 @@ k_step_warp(Ctl* ctl, Params p, StateBufs sb, Lists L, MeshDev mesh, double* for
     const uint32_t icl = warp_incl_scan(S.cnt[lane]);
     S.istart[lane + 1] = icl;
     __syncwarp();
-    const uint32_t my_a = S.istart[lane], my_b = S.istart[lane + 1];
 
     // B: contact law for 32 queued contacts at a time, then ordered
     // per-particle sums (a queued pair found apart by the exact test
@@ -162,12 +170,31 @@ k_step_warp(Ctl* ctl, Params p, StateBufs sb, Lists L, MeshDev mesh, double* for
 #pragma unroll
       for (int c = 0; c < 6; ++c) S.contrib[lane][c] = c6[c];
       __syncwarp();
-      const uint32_t a = my_a > i0 ? my_a : i0;
-      const uint32_t b = my_b < i0 + 32 ? my_b : i0 + 32;
-      for (uint32_t jj = a; jj < b; ++jj) acc.add(S.contrib[jj - i0]);
+      // the particles with contacts in this batch are pa .. pb (owner of a
+      // queue position: largest particle whose range starts at or before it)
+      const uint32_t last = (i0 + 32 < qn ? i0 + 32 : qn) - 1u;
+      int pa = 0, pb = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        if (S.istart[pa + step] <= i0) pa += step;
+        if (S.istart[pb + step] <= last) pb += step;
+      }
+      const int njobs = (pb - pa + 1) * 6;
+      for (int j = lane; j < njobs; j += 32) {
+        const int pp = pa + j / 6, c = j % 6;
+        const uint32_t ra = S.istart[pp], rb = S.istart[pp + 1];
+        const uint32_t a = ra > i0 ? ra : i0;
+        const uint32_t b = rb < i0 + 32 ? rb : i0 + 32;
+        CT h = S.acc_h[pp][c], l = S.acc_l[pp][c];
+        for (uint32_t jj = a; jj < b; ++jj) Pol::Acc::add1(h, l, S.contrib[jj - i0][c]);
+        S.acc_h[pp][c] = h;
+        S.acc_l[pp][c] = l;
+      }
       __syncwarp();
     }
   } while (e0 < E);
+  __syncwarp();
+  acc.set(S.acc_h[lane], S.acc_l[lane]);
 
   // M: particle-element contacts of the warp's particles, 32 candidates at a
   // time (all lanes busy), then ordered sums as in B: every lane adds the

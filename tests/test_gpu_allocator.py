@@ -38,7 +38,7 @@ def run(dem, s, steps, **kw):
 
 def test_torch_allocator_runs_bitwise_alike_and_returns_its_memory(env):
     torch, dem = env
-    s = scenes.drum_scene(n=20_000, seed=5)
+    s = scenes.drum_scene(n=20_000, seed=5, nn_dist=2.15e-3, speed=0.02)
     ref, a = run(dem, s, 300)
     ref.close()
     torch.cuda.synchronize()
@@ -57,7 +57,7 @@ def test_torch_allocator_runs_bitwise_alike_and_returns_its_memory(env):
 
 def test_failing_allocator_reports_nomem_and_gets_every_block_back(env):
     torch, dem = env
-    s = scenes.drum_scene(n=5_000, seed=5)
+    s = scenes.drum_scene(n=5_000, seed=5, nn_dist=2.15e-3, speed=0.02)
 
     class RunsDry(dem.TorchAllocator):
         def __init__(self, k):
