@@ -42,20 +42,33 @@ def neighbours(x, cutoff):
     return off, nbr
 
 
-def forward(W: dict, nf, ef, dst, nbr, n):
-    """W: name -> float64 tensor [inputs incl. the constant column][outputs]."""
+def bf16(t):
+    """Round to the nearest bfloat16 (ties to even), kept as float64."""
+    return t.to(torch.bfloat16).to(torch.float64)
+
+
+def forward(W: dict, nf, ef, dst, nbr, n, stored_bf16=False):
+    """W: name -> float64 tensor [inputs incl. the constant column][outputs].
+
+    stored_bf16: the network as the surrogate stores it, every layer input
+    (node and edge features, the node states entering a layer, the edge
+    states, the summed messages) rounded to bfloat16 where it is stored,
+    the products and sums in float64 (the weights are passed rounded)."""
     relu = torch.relu
+    r = bf16 if stored_bf16 else (lambda t: t)
+    nf, ef = r(nf), r(ef)
     h = relu(nf @ W["node"])
-    e = relu(ef @ W["edge"])
+    e = r(relu(ef @ W["edge"]))
     one = torch.zeros((e.shape[0], 16), dtype=torch.float64)
     one[:, 0] = 1.0
     onen = torch.zeros((n, 16), dtype=torch.float64)
     onen[:, 0] = 1.0
-    for r in range(ROUNDS):
-        m = relu(torch.cat([h[dst], h[nbr], e, one], 1) @ W[f"msg{r}"])
+    for k in range(ROUNDS):
+        hs = r(h)
+        m = relu(torch.cat([hs[dst], hs[nbr], e, one], 1) @ W[f"msg{k}"])
         M = torch.zeros((n, H), dtype=torch.float64).index_add_(0, dst, m)
-        h = h + relu(torch.cat([h, M, onen], 1) @ W[f"upd{r}"])
-    return torch.cat([h, onen], 1) @ W["dec"]
+        h = h + relu(torch.cat([hs, r(M), onen], 1) @ W[f"upd{k}"])
+    return torch.cat([r(h), onen], 1) @ W["dec"]
 
 
 def loss_and_grads(weights: dict, nf, ef, dst, nbr, target):

@@ -100,6 +100,32 @@ def test_forward_and_gradients_match_the_fp64_network(sg):
         assert err < 6e-2, (name, err)
 
 
+def test_forward_matches_the_network_as_stored_in_bf16(sg):
+    # the oracle rounding every stored layer input to bfloat16 where the
+    # kernels store it: what remains is the FP32 accumulation of the GEMMs and
+    # sums (and the rare bfloat16 rounding that it flips)
+    mo = pytest.importorskip("oracle.mpnn_oracle")
+    import torch
+    s = small_state()
+    R = s["R"]
+    model = sg.MPNN(seed=3)
+    g = sg.make_graph(s["x"], s["v"], s["w"], R, R.max())
+    W = {k: torch.tensor(bf16(v)[0].astype(np.float64)) for k, v in model.weights().items()}
+    off, nbr, dst = g.edges_host()
+    nf, ef, dst_r = mo.features(s["x"], s["v"], s["w"], R, off, nbr, sg.SCALES["vs"],
+                                sg.SCALES["Rs"])
+    args = (torch.tensor(nf), torch.tensor(ef), torch.tensor(dst_r), torch.tensor(nbr), g.n)
+    y_b = mo.forward(W, *args, stored_bf16=True)[:, :6].numpy()
+    y_f = mo.forward(W, *args)[:, :6].numpy()
+    y = model.forward(g)[:g.n, :6].cpu().numpy()
+    err = np.abs(y - y_b).max() / np.abs(y_b).max()
+    err_f = np.abs(y - y_f).max() / np.abs(y_f).max()
+    print(f"surrogate forward against the bf16-stored oracle {err:.2e}, "
+          f"against the unrounded one {err_f:.2e}")
+    assert err <= 5e-3, err
+    assert err < err_f
+
+
 def test_training_reduces_the_loss(sg):
     s = small_state(n=600, seed=5)
     R = s["R"]

@@ -70,3 +70,38 @@ def test_decoder_bias_alone_is_the_output():
     W["dec"][128, :6] = b
     _, y, _ = mo.loss_and_grads(W, nf, ef, dst, nbr, T)
     assert np.array_equal(y, np.tile(b, (nf.shape[0], 1)))
+
+
+def test_stored_bf16_forward_rounds_only_where_it_stores():
+    # on values that bfloat16 holds exactly rounding the stored layer inputs
+    # changes nothing; on general values it moves the output by about
+    # bfloat16's relative precision, not more
+    W, nf, ef, dst, nbr, T = small_case(seed=3)
+    n = nf.shape[0]
+    args = (torch.tensor(dst), torch.tensor(nbr), n)
+    Wt = {k: torch.tensor(v) for k, v in W.items()}
+    y = mo.forward(Wt, torch.tensor(nf), torch.tensor(ef), *args)
+    yb = mo.forward(Wt, torch.tensor(nf), torch.tensor(ef), *args, stored_bf16=True)
+    rel = float((yb - y).abs().max() / y.abs().max())
+    assert 1e-5 < rel < 5e-2, rel
+    # exact case: every layer output copies one of its inputs (one weight 1
+    # per output column), features are 0, 1 or 2, messages copy edge states
+    # or the constant, so every value is an integer far below 256
+    rng = np.random.default_rng(5)
+    H = mo.H
+
+    def copies(kin, kout, lo=0, hi=None):
+        w = np.zeros((kin, kout))
+        w[rng.integers(lo, hi if hi is not None else kin, size=kout), np.arange(kout)] = 1.0
+        return torch.tensor(w)
+
+    Wi = {"node": copies(16, H), "edge": copies(16, H), "dec": copies(H + 16, 64)}
+    for r in range(3):
+        Wi[f"msg{r}"] = copies(3 * H + 16, H, 2 * H, 3 * H + 1)  # edge states or the constant
+        Wi[f"upd{r}"] = copies(2 * H + 16, H, 0, 2 * H + 1)
+    nfi = torch.tensor(rng.integers(0, 3, size=nf.shape).astype(np.float64))
+    efi = torch.tensor(rng.integers(0, 3, size=ef.shape).astype(np.float64))
+    y0 = mo.forward(Wi, nfi, efi, *args)
+    y1 = mo.forward(Wi, nfi, efi, *args, stored_bf16=True)
+    assert 0 < float(y0.abs().max()) < 256
+    assert torch.equal(y0, y1)
