@@ -118,12 +118,16 @@ def test_forward_matches_the_network_as_stored_in_bf16(sg):
     y_b = mo.forward(W, *args, stored_bf16=True)[:, :6].numpy()
     y_f = mo.forward(W, *args)[:, :6].numpy()
     y = model.forward(g)[:g.n, :6].cpu().numpy()
-    err = np.abs(y - y_b).max() / np.abs(y_b).max()
-    err_f = np.abs(y - y_f).max() / np.abs(y_f).max()
-    print(f"surrogate forward against the bf16-stored oracle {err:.2e}, "
-          f"against the unrounded one {err_f:.2e}")
-    assert err <= 5e-3, err
-    assert err < err_f
+    scale = np.abs(y_b).max()
+    d_b = np.abs(y - y_b) / scale
+    d_f = np.abs(y - y_f) / scale
+    print("surrogate forward against the bf16-stored oracle: max %.2e median %.2e; "
+          "against the unrounded one: max %.2e median %.2e"
+          % (d_b.max(), np.median(d_b), d_f.max(), np.median(d_f)))
+    # a bfloat16 rounding that the FP32 sums flip moves single values by
+    # 2^-8 of themselves; the typical output matches far closer
+    assert d_b.max() <= 5e-3, d_b.max()
+    assert np.median(d_b) < 0.5 * np.median(d_f), (np.median(d_b), np.median(d_f))
 
 
 def test_training_reduces_the_loss(sg):
