@@ -126,8 +126,10 @@ def test_forward_matches_the_network_as_stored_in_bf16(sg):
           % (d_b.max(), np.median(d_b), d_f.max(), np.median(d_f)))
     # a bfloat16 rounding that the FP32 sums flip moves single values by
     # 2^-8 of themselves; the typical output matches far closer
+    # (measured: median 5.8e-8 against 4.3e-4 for the unrounded network)
     assert d_b.max() <= 5e-3, d_b.max()
-    assert np.median(d_b) < 0.5 * np.median(d_f), (np.median(d_b), np.median(d_f))
+    assert np.median(d_b) <= 1e-5, np.median(d_b)
+    assert np.median(d_b) < 0.01 * np.median(d_f), (np.median(d_b), np.median(d_f))
 
 
 def test_training_reduces_the_loss(sg):
