@@ -938,6 +938,7 @@ int dem_scene_create_with_allocator(const dem_params* params, const dem_particle
     ListBuf& lb = s->L.b[b];
     lb.gid = M.get<uint32_t>(n);
     lb.posf = M.get<float4>(n);
+    if (!p.mixed && !p.mixed64) lb.inv = M.get<D4>(n);
     lb.meta = M.get<uint32_t>(n);
     lb.offs = M.get<uint32_t>(n + 1);
     lb.nbr = M.get<uint32_t>((size_t)p.cap * n);

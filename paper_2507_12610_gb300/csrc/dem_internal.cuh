@@ -159,7 +159,13 @@ struct ListBuf {
                     // the partner's entry for the same pair (one evaluation per pair)
   uint8_t* back;    // [offs[n]] for an entry whose partner has the higher caller index,
                     // the index of this particle in the partner's list
+  D4* inv;          // [n] DEM_FP64 only (else null): 1/R, 1/m, 1/I of the particle in
+                    // each slot, the divisions of the law done once per rebuild
 };
+
+// Per-particle data a policy's contact law reads beside the state records
+// (DEM_FP64: the inverses of ListBuf::inv; the other policies: nothing).
+struct NoAux {};
 
 // Mesh elements (Sec. 3.3): triangles first, then points, segments and
 // rectangles; four vertex slots per element, unused slots repeat vertex 0.
@@ -261,6 +267,7 @@ __device__ __forceinline__ ListBuf list_of(const Lists& L, uint32_t b) {
   r.hpm = b ? L.b[1].hpm : L.b[0].hpm;
   r.mir = b ? L.b[1].mir : L.b[0].mir;
   r.back = b ? L.b[1].back : L.b[0].back;
+  r.inv = b ? L.b[1].inv : L.b[0].inv;
   return r;
 }
 #endif

@@ -45,6 +45,19 @@ __device__ __forceinline__ float4 posf_of(const Params& p, const void* state, ui
                      (float)(P.z - p.origin[2]), (float)P.w);
 }
 
+// 1/R, 1/m and 1/I of a DEM_FP64 particle, each division written as the
+// step's law and integrator write it, so with the same bits; zero for a row
+// awaiting spawning.  (Only DEM_FP64 keeps them.)
+__device__ __forceinline__ D4 inverses(const D4& P, const D4& V) {
+  const double R = P.w, mass = V.w;
+  if (R == 0.0) return make_D4(0.0, 0.0, 0.0, 0.0);
+  const double I = 2.0 / 5.0 * mass * R * R;
+  return make_D4(1.0 / R, 1.0 / mass, 1.0 / I, 0.0);
+}
+__device__ __forceinline__ D4 inverses(const F8&, const F8&) {
+  return make_D4(0.0, 0.0, 0.0, 0.0);
+}
+
 __global__ void k_clear(const Ctl* ctl, uint32_t* a, int64_t n) {
   if (!rebuilding(ctl)) return;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -130,6 +143,8 @@ k_permute(const Ctl* ctl, Params p, BinBuf bb, StateBufs sb, Lists L) {
   Q1[t] = Q0[s];
   gid_new[t] = gid_old[s];
   posf_new[t] = posf_of(p, P0, s);
+  D4* inv_new = list_of(L, lph ^ 1u).inv;
+  if (inv_new) inv_new[t] = inverses(P0[s], V0[s]);
 }
 
 // ---- triangle cell lists -----------------------------------------------------

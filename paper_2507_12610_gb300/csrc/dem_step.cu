@@ -30,21 +30,31 @@ namespace {
 // One thread per element: its vertices at the pose of step ctl->step + ahead
 // (absolute in FP64; shifted as hi + lo floats), and for triangles and
 // rectangles the unit normal (the reference normal, rotated) and offset of
-// its plane, split the same way.
-__global__ void k_mesh_pose(const Ctl* ctl, Params p, MeshDev mesh, int ahead) {
-  if (ctl->status) return;
+// its plane, split the same way.  The rotation's cosine and sine are taken
+// once per block.
+constexpr int kPoseThreads = 128;
+
+__global__ void __launch_bounds__(kPoseThreads)
+k_mesh_pose(const Ctl* ctl, Params p, MeshDev mesh, int ahead) {
+  __shared__ double s_cs[2];
+  if (ctl->status) return;  // the same for every thread of the block
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= mesh.nt) return;
   const int64_t step = ctl->step + ahead;
+  if (threadIdx.x == 0) {
+    // the pose of this step: the same expression, so the same bits, as
+    // k_set_pose, which keeps the one-thread step kernels free of FP64
+    // transcendentals
+    const double th = p.omega_norm * ((double)step * p.dt);
+    s_cs[0] = p.omega_norm > 0.0 ? cos(th) : 1.0;
+    s_cs[1] = p.omega_norm > 0.0 ? sin(th) : 0.0;
+  }
+  __syncthreads();
+  if (k >= mesh.nt) return;
   const int4 tv = mesh.tri[k];
   const int nvk = tv.w >= 0 ? 4 : (tv.z >= 0 ? 3 : (tv.y >= 0 ? 2 : 1));
   const double rad = mesh.rad[k];
   const double wn = p.omega_norm;
-  // the pose of this step; every thread evaluates the same expression (the
-  // same bits as k_set_pose), which keeps the one-thread step kernels free of
-  // FP64 transcendentals
-  const double th = p.omega_norm * ((double)step * p.dt);
-  const double c = wn > 0.0 ? cos(th) : 1.0, s = wn > 0.0 ? sin(th) : 0.0;
+  const double c = s_cs[0], s = s_cs[1];
   const V3<double> ax =
       wn > 0.0 ? (1.0 / wn) * mk(p.mesh_omega[0], p.mesh_omega[1], p.mesh_omega[2])
                : mk(0.0, 0.0, 0.0);
@@ -240,6 +250,8 @@ struct MixedPolicy {
   using Rec = F8;
   using Hist = HistM;
   using T = float;
+  using Aux = NoAux;  // the records carry 1/R and 1/m
+  static __device__ __forceinline__ Aux aux(const ListBuf&, uint32_t) { return Aux{}; }
 
   struct Acc {
     Acc3 F, T;
@@ -311,11 +323,12 @@ struct MixedPolicy {
   // to c6 and returns true.
   static __device__ __forceinline__ bool pair(const Params& p, bool t_is_i, const F8& Pi,
                                               const F8& Pj, const F8& Vi, const F8& Vj,
-                                              const F8& Wi, const F8& Wj, HistM& h,
-                                              uint32_t stamp_now, uint32_t stamp_new,
-                                              float c6[6]) {
+                                              const F8& Wi, const F8& Wj, const Aux& Ai,
+                                              const Aux& Aj, HistM& h, uint32_t stamp_now,
+                                              uint32_t stamp_new, float c6[6]) {
     LawOut<float> o;
-    if (!pair_law(p, Pi, Pj, Vi, Vj, Wi, Wj, h, stamp_now, stamp_new, o)) return false;
+    if (!pair_law(p, Pi, Pj, Vi, Vj, Wi, Wj, Ai, Aj, h, stamp_now, stamp_new, o))
+      return false;
     if (t_is_i) {
       c6[0] = o.f.x; c6[1] = o.f.y; c6[2] = o.f.z;
       c6[3] = o.ti.x; c6[4] = o.ti.y; c6[5] = o.ti.z;
@@ -330,8 +343,9 @@ struct MixedPolicy {
   // and returns the force on i and the torques on i and j.
   static __device__ __forceinline__ bool pair_law(const Params& p, const F8& Pi, const F8& Pj,
                                                   const F8& Vi, const F8& Vj, const F8& Wi,
-                                                  const F8& Wj, HistM& h, uint32_t stamp_now,
-                                                  uint32_t stamp_new, LawOut<float>& o) {
+                                                  const F8& Wj, const Aux& Ai, const Aux& Aj,
+                                                  HistM& h, uint32_t stamp_now, uint32_t stamp_new,
+                                                  LawOut<float>& o) {
     Geo g;
     if (!touch(p, Pi, Pj, g)) return false;
     LawConst<float> cpp{p.f_Es_pp, p.f_Gs_pp, p.f_beta, p.f_mu_s, p.f_mu_r, p.f_mu_t, p.f_dt,
@@ -544,6 +558,8 @@ struct Mixed64Policy {
   using Hist = HistM;
   using T = float;
   using Acc = MixedPolicy::Acc;
+  using Aux = NoAux;
+  static __device__ __forceinline__ Aux aux(const ListBuf&, uint32_t) { return Aux{}; }
 
   // Conservative pre-test: the offset in FP64, the comparison in FP32 with a
   // 1e-4 relative margin (symmetric in its arguments).
@@ -555,11 +571,12 @@ struct Mixed64Policy {
 
   static __device__ __forceinline__ bool pair(const Params& p, bool t_is_i, const D4& Pi,
                                               const D4& Pj, const D4& Vi, const D4& Vj,
-                                              const D4& Wi, const D4& Wj, HistM& h,
-                                              uint32_t stamp_now, uint32_t stamp_new,
-                                              float c6[6]) {
+                                              const D4& Wi, const D4& Wj, const Aux& Ai,
+                                              const Aux& Aj, HistM& h, uint32_t stamp_now,
+                                              uint32_t stamp_new, float c6[6]) {
     LawOut<float> o;
-    if (!pair_law(p, Pi, Pj, Vi, Vj, Wi, Wj, h, stamp_now, stamp_new, o)) return false;
+    if (!pair_law(p, Pi, Pj, Vi, Vj, Wi, Wj, Ai, Aj, h, stamp_now, stamp_new, o))
+      return false;
     if (t_is_i) {
       c6[0] = o.f.x; c6[1] = o.f.y; c6[2] = o.f.z;
       c6[3] = o.ti.x; c6[4] = o.ti.y; c6[5] = o.ti.z;
@@ -576,8 +593,9 @@ struct Mixed64Policy {
   // in FP64 before rounding, so they keep their relative accuracy.
   static __device__ __forceinline__ bool pair_law(const Params& p, const D4& Pi, const D4& Pj,
                                                   const D4& Vi, const D4& Vj, const D4& Wi,
-                                                  const D4& Wj, HistM& h, uint32_t stamp_now,
-                                                  uint32_t stamp_new, LawOut<float>& o) {
+                                                  const D4& Wj, const Aux& Ai, const Aux& Aj,
+                                                  HistM& h, uint32_t stamp_now, uint32_t stamp_new,
+                                                  LawOut<float>& o) {
     const double dx = Pi.x - Pj.x, dy = Pi.y - Pj.y, dz = Pi.z - Pj.z;
     const double d2 = dx * dx + dy * dy + dz * dz;
     const double S = Pi.w + Pj.w;
@@ -765,8 +783,8 @@ struct Mixed64Policy {
 
 void launch_mesh_pose(cudaStream_t st, const Ctl* ctl, const Params& p, MeshDev mesh, int ahead) {
   if (mesh.nt <= 0) return;
-  // small blocks spread the elements over many SMs (the kernel is FP64 latency)
-  k_mesh_pose<<<(unsigned)((mesh.nt + 31) / 32), 32, 0, st>>>(ctl, p, mesh, ahead);
+  k_mesh_pose<<<(unsigned)((mesh.nt + kPoseThreads - 1) / kPoseThreads), kPoseThreads, 0, st>>>(
+      ctl, p, mesh, ahead);
 }
 
 void launch_step(cudaStream_t st, Ctl* ctl, const Params& p, StateBufs sb, Lists L,

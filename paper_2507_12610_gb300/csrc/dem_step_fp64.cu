@@ -30,6 +30,8 @@ struct Fp64Policy {
   using Rec = D4;
   using Hist = HistD;
   using T = double;
+  using Aux = D4;  // 1/R, 1/m, 1/I of the particle (ListBuf::inv)
+  static __device__ __forceinline__ Aux aux(const ListBuf& lb, uint32_t s) { return lb.inv[s]; }
 
   struct Acc {
     V3<double> F, T;
@@ -77,11 +79,12 @@ struct Fp64Policy {
 
   static __device__ __forceinline__ bool pair(const Params& p, bool t_is_i, const D4& Pi,
                                               const D4& Pj, const D4& Vi, const D4& Vj,
-                                              const D4& Wi, const D4& Wj, HistD& h,
-                                              uint32_t stamp_now, uint32_t stamp_new,
-                                              double c6[6]) {
+                                              const D4& Wi, const D4& Wj, const Aux& Ai,
+                                              const Aux& Aj, HistD& h, uint32_t stamp_now,
+                                              uint32_t stamp_new, double c6[6]) {
     LawOut<double> o;
-    if (!pair_law(p, Pi, Pj, Vi, Vj, Wi, Wj, h, stamp_now, stamp_new, o)) return false;
+    if (!pair_law(p, Pi, Pj, Vi, Vj, Wi, Wj, Ai, Aj, h, stamp_now, stamp_new, o))
+      return false;
     if (t_is_i) {
       c6[0] = o.f.x; c6[1] = o.f.y; c6[2] = o.f.z;
       c6[3] = o.ti.x; c6[4] = o.ti.y; c6[5] = o.ti.z;
@@ -96,8 +99,9 @@ struct Fp64Policy {
   // and returns the force on i and the torques on i and j.
   static __device__ __forceinline__ bool pair_law(const Params& p, const D4& Pi, const D4& Pj,
                                                   const D4& Vi, const D4& Vj, const D4& Wi,
-                                                  const D4& Wj, HistD& h, uint32_t stamp_now,
-                                                  uint32_t stamp_new, LawOut<double>& o) {
+                                                  const D4& Wj, const Aux& Ai, const Aux& Aj,
+                                                  HistD& h, uint32_t stamp_now, uint32_t stamp_new,
+                                                  LawOut<double>& o) {
     Geo g;
     if (!touch(p, Pi, Pj, g)) return false;
     LawConst<double> cpp{p.Es_pp, p.Gs_pp, p.beta, p.mu_s, p.mu_r, p.mu_t, p.dt, p.cs_cn_pp};
@@ -112,9 +116,10 @@ struct Fp64Policy {
     // the printed forms, in their order of operations: in a settled
     // bed the per-particle torque sums cancel to a small fraction of their
     // terms, so an algebraically equal form (R_i R_j / (R_i + R_j)) would
-    // amplify its last-bit differences past the 1e-12 bound
-    const double Rs = 1.0 / (1.0 / Ri + 1.0 / Rj);
-    const double ms = 1.0 / (1.0 / Vi.w + 1.0 / Vj.w);
+    // amplify its last-bit differences past the 1e-12 bound; 1/R and 1/m
+    // come from the rebuild (the same divisions, done once per particle)
+    const double Rs = 1.0 / (Ai.x + Aj.x);
+    const double ms = 1.0 / (Ai.y + Aj.y);
     const double ri = Ri - g.delta / 2.0, rj = Rj - g.delta / 2.0;
     V3<double> us = mk(0.0, 0.0, 0.0), ur = us;
     double ut = 0.0;
@@ -218,14 +223,14 @@ struct Fp64Policy {
       ++nmesh;
     }
     // semi-implicit Euler + SPIRAL (Sec. 2.3)
-    const double R = Pt.w, mass = Vt.w;
-    const double I = 2.0 / 5.0 * mass * R * R;
+    const double R = Pt.w, mass = Vt.w;  // I = 2/5 m R^2
     const double ci = 9.0 * p.eta / (2.0 * p.rho * R * R);
     const double gi = 10.0 / 3.0 * ci;
     V3<double> v = xyz(Vt), w = xyz(Wt), x = xyz(Pt);
     const V3<double> g = mk(p.g[0], p.g[1], p.g[2]);
-    const V3<double> a = (1.0 / mass) * F + g - ci * v;
-    const V3<double> al = (1.0 / I) * T - gi * w;
+    const D4 iv = lb.inv[t];  // 1.0 / mass and 1.0 / I, from the rebuild
+    const V3<double> a = iv.y * F + g - ci * v;
+    const V3<double> al = iv.z * T - gi * w;
     v = v + p.dt * a;
     x = x + p.dt * v;
     const D4 q4 = Q[t];

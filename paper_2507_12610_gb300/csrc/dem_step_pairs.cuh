@@ -159,8 +159,8 @@ k_pairs(Ctl* ctl, Params p, StateBufs sb, Lists L, PairOut<typename Pol::T>* res
         const int tl = qlane[i];
         Hist h = Hh[ent];
         LawOut<CT> o;
-        if (Pol::pair_law(p, P[w0 + tl], P[u], V[w0 + tl], V[u], W[w0 + tl], W[u], h,
-                          stamp_now, stamp_new, o)) {
+        if (Pol::pair_law(p, P[w0 + tl], P[u], V[w0 + tl], V[u], W[w0 + tl], W[u],
+                          Pol::aux(lb, w0 + tl), Pol::aux(lb, u), h, stamp_now, stamp_new, o)) {
           Hh[ent] = h;
           put_out(res + ent, o);
           atomicOr(&touch[w0 + tl], 1ull << qk[i]);

@@ -159,10 +159,11 @@ k_step_warp(Ctl* ctl, Params p, StateBufs sb, Lists L, MeshDev mesh, double* for
         const Rec Pt = P[w0 + tl], Pu = P[u];
         const Rec Vt = V[w0 + tl], Vu = V[u];
         const Rec Wt = W[w0 + tl], Wu = W[u];
+        const typename Pol::Aux At = Pol::aux(lb, w0 + tl), Au = Pol::aux(lb, u);
         Hist h = H[e];
         if (Pol::pair(p, t_is_i, t_is_i ? Pt : Pu, t_is_i ? Pu : Pt, t_is_i ? Vt : Vu,
-                      t_is_i ? Vu : Vt, t_is_i ? Wt : Wu, t_is_i ? Wu : Wt, h, stamp_now,
-                      stamp_new, c6)) {
+                      t_is_i ? Vu : Vt, t_is_i ? Wt : Wu, t_is_i ? Wu : Wt, t_is_i ? At : Au,
+                      t_is_i ? Au : At, h, stamp_now, stamp_new, c6)) {
           H[e] = h;
           ++npair;
         }
