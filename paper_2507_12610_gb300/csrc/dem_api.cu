@@ -974,7 +974,7 @@ int dem_scene_create_with_allocator(const dem_params* params, const dem_particle
   if (has_mesh) {
     s->bb.tcell_count = M.get<uint32_t>(ncells);
     s->bb.tcell_start = M.get<uint32_t>(ncells + 1);
-    s->bb.tcell_overflow = M.get<uint32_t>(1);
+    s->bb.tcell_overflow = M.get<uint32_t>(2);  // [1]: element lists of a still mesh built
     // capacity: for every element, the cells of a cube around its bounding
     // ball grown by the reach (valid for any pose of a rigid mesh)
     const double reach = rmax + skin + 2.0 * p.list_margin;
@@ -1049,6 +1049,8 @@ int dem_scene_create_with_allocator(const dem_params* params, const dem_particle
     p.mat_d = md;
   }
   if (M.failed) return fail(DEM_ERR_NOMEM);
+  if (has_mesh && cudaMemset(s->bb.tcell_overflow, 0, 2 * sizeof(uint32_t)) != cudaSuccess)
+    return fail(DEM_ERR_CUDA);
   s->mesh.nv = s->nv;
   s->mesh.nt = s->nt;
 

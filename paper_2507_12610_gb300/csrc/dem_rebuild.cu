@@ -58,11 +58,27 @@ __device__ __forceinline__ D4 inverses(const F8&, const F8&) {
   return make_D4(0.0, 0.0, 0.0, 0.0);
 }
 
+// The element cell lists of a mesh that does not turn are built at the first
+// rebuild and kept (the elements and the grid stay put); bb.tcell_overflow[1]
+// marks them built.  Only the scan of their counts runs again, to the same
+// offsets.
+__device__ __forceinline__ bool tcells_kept(const Params& p, const BinBuf& bb) {
+  return p.omega_norm == 0.0 && bb.tcell_overflow[1] != 0u;
+}
+
 __global__ void k_clear(const Ctl* ctl, uint32_t* a, int64_t n) {
   if (!rebuilding(ctl)) return;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     a[i] = 0u;
+}
+
+// k_clear of the element counts, skipped while the lists are kept
+__global__ void k_clear_tcells(const Ctl* ctl, Params p, BinBuf bb) {
+  if (!rebuilding(ctl) || tcells_kept(p, bb)) return;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.ncells;
+       i += (int64_t)gridDim.x * blockDim.x)
+    bb.tcell_count[i] = 0u;
 }
 
 // key = cell of each particle; local = its arrival index in the cell.
@@ -155,7 +171,7 @@ k_permute(const Ctl* ctl, Params p, BinBuf bb, StateBufs sb, Lists L) {
 // counts, pass 1 fills.  blockIdx.x is the element; its cells are shared by
 // the gridDim.y blocks of that element.
 __global__ void k_tri_cells(const Ctl* ctl, Params p, MeshDev mesh, BinBuf bb, int pass) {
-  if (!rebuilding(ctl)) return;
+  if (!rebuilding(ctl) || tcells_kept(p, bb)) return;
   const int k = blockIdx.x;
   if (k >= mesh.nt) return;
   const float4 A = mesh.curf[4 * k], B = mesh.curf[4 * k + 1], C = mesh.curf[4 * k + 2],
@@ -225,7 +241,7 @@ constexpr int kSortMax = 512;  // longer lists (not met in practice) sort serial
 __global__ void __launch_bounds__(32 * kSortWarps)
 k_tri_cell_sort(const Ctl* ctl, Params p, BinBuf bb) {
   __shared__ uint32_t buf_s[kSortWarps][kSortMax];
-  if (!rebuilding(ctl)) return;
+  if (!rebuilding(ctl) || tcells_kept(p, bb)) return;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   uint32_t* buf = buf_s[wib];
   const int64_t nw = (int64_t)gridDim.x * kSortWarps;
@@ -475,8 +491,9 @@ __global__ void k_rebuild_prep(Ctl* ctl) {
   ctl->max_list_len = 0;
 }
 
-__global__ void k_rebuild_end(Ctl* ctl, Params p) {
+__global__ void k_rebuild_end(Ctl* ctl, Params p, BinBuf bb, int nt) {
   if (!rebuilding(ctl)) return;
+  if (nt > 0 && p.omega_norm == 0.0) bb.tcell_overflow[1] = 1u;  // element lists kept
   ctl->phase ^= 1u;
   ctl->lphase ^= 1u;
   ctl->rebuilds += 1;
@@ -532,11 +549,11 @@ void launch_rebuild(cudaStream_t st, Ctl* ctl, const Params& p, StateBufs sb, Li
   else
     k_permute<D4><<<nb, kThreads, 0, st>>>(ctl, p, bb, sb, L);
   if (mesh.nt > 0) {
-    k_clear<<<gcells, kThreads, 0, st>>>(ctl, bb.tcell_count, p.ncells);
+    k_clear_tcells<<<gcells, kThreads, 0, st>>>(ctl, p, bb);
     k_tri_cells<<<dim3((unsigned)mesh.nt, (unsigned)p.tri_chunks), 128, 0, st>>>(ctl, p, mesh, bb, 0);
     launch_scan(st, ctl, bb.tcell_count, bb.tcell_start, p.ncells, bb.block_sums);
     k_tri_cells_check<<<1, 1, 0, st>>>(ctl, p, bb);
-    k_clear<<<gcells, kThreads, 0, st>>>(ctl, bb.tcell_count, p.ncells);
+    k_clear_tcells<<<gcells, kThreads, 0, st>>>(ctl, p, bb);
     k_tri_cells<<<dim3((unsigned)mesh.nt, (unsigned)p.tri_chunks), 128, 0, st>>>(ctl, p, mesh, bb, 1);
     k_tri_cell_sort<<<152 * 8, 32 * kSortWarps, 0, st>>>(ctl, p, bb);
   }
@@ -553,7 +570,7 @@ void launch_rebuild(cudaStream_t st, Ctl* ctl, const Params& p, StateBufs sb, Li
   else
     k_list_compact<HistD><<<nbc, 32 * kCompactWarps, 0, st>>>(ctl, p, bb, L);
   if (p.pair_res) k_mirror<<<nb128, 128, 0, st>>>(ctl, p, L);
-  k_rebuild_end<<<1, 1, 0, st>>>(ctl, p);
+  k_rebuild_end<<<1, 1, 0, st>>>(ctl, p, bb, mesh.nt);
 }
 
 }  // namespace dem
