@@ -58,12 +58,35 @@ __device__ __forceinline__ D4 inverses(const F8&, const F8&) {
   return make_D4(0.0, 0.0, 0.0, 0.0);
 }
 
-// The element cell lists of a mesh that does not turn are built at the first
-// rebuild and kept (the elements and the grid stay put); bb.tcell_overflow[1]
-// marks them built.  Only the scan of their counts runs again, to the same
-// offsets.
-__device__ __forceinline__ bool tcells_kept(const Params& p, const BinBuf& bb) {
-  return p.omega_norm == 0.0 && bb.tcell_overflow[1] != 0u;
+// The element cell lists are built once, at the first rebuild, in the mesh's
+// own frame (the elements at the reference pose), and kept: the mesh is rigid
+// and the grid fixed.  A particle looks up the list of the cell that holds its
+// position turned back by the mesh's current rotation (distances to the
+// elements are the same in both frames).  bb.tcell_overflow[1] marks the lists
+// built.  Only the scan of their counts runs again, to the same offsets.
+__device__ __forceinline__ bool tcells_kept(const Params&, const BinBuf& bb) {
+  return bb.tcell_overflow[1] != 0u;
+}
+
+// Vertex slot j of element k at the reference pose, shifted and rounded like
+// the pose arrays (unused slots repeat vertex 0); w = the vertex count in slot 0.
+__device__ __forceinline__ float4 ref_vertex(const Params& p, const MeshDev& mesh, int4 tv,
+                                             int nvk, int j) {
+  const int vi = j < nvk ? (j == 0 ? tv.x : (j == 1 ? tv.y : (j == 2 ? tv.z : tv.w))) : tv.x;
+  const D4 r = mesh.ref[vi];
+  return make_float4((float)(r.x - p.origin[0]), (float)(r.y - p.origin[1]),
+                     (float)(r.z - p.origin[2]), j == 0 ? (float)nvk : 0.f);
+}
+
+// A shifted position turned back into the mesh's reference frame: the
+// rotation by -theta (cos c, sin s) about the axis through the mesh centre.
+__device__ __forceinline__ V3<float> to_mesh_frame(const Params& p, V3<float> q, float c,
+                                                   float s) {
+  const float wn = (float)p.omega_norm;
+  const V3<float> ax = mk(p.f_omega[0] / wn, p.f_omega[1] / wn, p.f_omega[2] / wn);
+  const V3<float> cen = mk(p.center_hi[0], p.center_hi[1], p.center_hi[2]);
+  const V3<float> r = q - cen;
+  return cen + (c * r - s * cross(ax, r) + ((1.f - c) * dot(ax, r)) * ax);
 }
 
 __global__ void k_clear(const Ctl* ctl, uint32_t* a, int64_t n) {
@@ -165,18 +188,20 @@ k_permute(const Ctl* ctl, Params p, BinBuf bb, StateBufs sb, Lists L) {
 
 // ---- triangle cell lists -----------------------------------------------------
 
-// Cells within reach of triangle k: its bounding box grown by the reach
-// R_k + R_max + skin (+ margin), then a conservative per-cell test: the cell
-// centre within reach + half the cell diagonal of the triangle.  pass 0
-// counts, pass 1 fills.  blockIdx.x is the element; its cells are shared by
+// Cells within reach of element k at the reference pose: its bounding box
+// grown by the reach R_k + R_max + skin (+ margin), then a conservative
+// per-cell test: the cell centre within reach + half the cell diagonal of the
+// element.  pass 0 counts, pass 1 fills.  blockIdx.x is the element; its cells are shared by
 // the gridDim.y blocks of that element.
 __global__ void k_tri_cells(const Ctl* ctl, Params p, MeshDev mesh, BinBuf bb, int pass) {
   if (!rebuilding(ctl) || tcells_kept(p, bb)) return;
   const int k = blockIdx.x;
   if (k >= mesh.nt) return;
-  const float4 A = mesh.curf[4 * k], B = mesh.curf[4 * k + 1], C = mesh.curf[4 * k + 2],
-               D = mesh.curf[4 * k + 3];
-  const int nvk = (int)A.w;
+  // the reference pose (the lists are in the mesh's frame)
+  const int4 tv = mesh.tri[k];
+  const int nvk = tv.w >= 0 ? 4 : (tv.z >= 0 ? 3 : (tv.y >= 0 ? 2 : 1));
+  const float4 A = ref_vertex(p, mesh, tv, nvk, 0), B = ref_vertex(p, mesh, tv, nvk, 1),
+               C = ref_vertex(p, mesh, tv, nvk, 2), D = ref_vertex(p, mesh, tv, nvk, 3);
   const float reach = (float)mesh.rad[k] + p.rmax + p.skin + p.list_margin;
   // unused vertex slots repeat vertex 0, so the box of all four is the element's
   const float3 lo = make_float3(fminf(fminf(A.x, B.x), fminf(C.x, D.x)) - reach,
@@ -385,7 +410,14 @@ k_list_build(Ctl* ctl, Params p, BinBuf bb, Lists L, MeshDev mesh) {
   const int nt_o = (int)((mo >> 16) & 0xffu);
   int ntc = 0;
   if (mesh.nt > 0) {
-    const uint32_t cell = cell_index(p, c);
+    // the element list of the particle's cell in the mesh's frame
+    int3 cm = c;
+    if (p.omega_norm > 0.0) {
+      const V3<float> qm = to_mesh_frame(p, mk(X.x, X.y, X.z), (float)ctl->rot_c,
+                                         (float)ctl->rot_s);
+      cm = cell_coords(p, qm.x, qm.y, qm.z);
+    }
+    const uint32_t cell = cell_index(p, cm);
     const uint32_t a = bb.tcell_start[cell], b = min(bb.tcell_start[cell + 1], bb.tcap);
     const Hist* hpm_o = static_cast<const Hist*>(lo.hpm);
     Hist* hpm_n = static_cast<Hist*>(ln.hpm);
@@ -423,9 +455,9 @@ k_list_build(Ctl* ctl, Params p, BinBuf bb, Lists L, MeshDev mesh) {
 
 // Pack the new pair lists into CSR form (offsets from the scan of the counts)
 // and copy each pair's friction history record from the previous list where
-// k_list_build found one and the contact touched in the previous step.  A warp covers the entries of 32 consecutive slots,
-// 32 entries at a time (all lanes busy, consecutive entries written by
-// consecutive lanes).
+// k_list_build found one and the contact touched in the previous step.  A
+// warp covers the entries of 32 consecutive slots, 32 entries at a time (all
+// lanes busy, consecutive entries written by consecutive lanes).
 constexpr int kCompactWarps = 4;
 
 __device__ __forceinline__ uint32_t warp_scan_incl(uint32_t v) {
@@ -484,8 +516,13 @@ k_list_compact(Ctl* ctl, Params p, BinBuf bb, Lists L) {
   }
 }
 
-__global__ void k_rebuild_prep(Ctl* ctl) {
+__global__ void k_rebuild_prep(Ctl* ctl, Params p) {
   if (!rebuilding(ctl)) return;
+  if (p.omega_norm > 0.0) {  // the rotation of this step, for the mesh-frame lookups
+    const double th = p.omega_norm * ((double)ctl->step * p.dt);
+    ctl->rot_c = cos(th);
+    ctl->rot_s = sin(th);
+  }
   ctl->list_entries = 0;
   ctl->mesh_candidates = 0;
   ctl->max_list_len = 0;
@@ -493,7 +530,7 @@ __global__ void k_rebuild_prep(Ctl* ctl) {
 
 __global__ void k_rebuild_end(Ctl* ctl, Params p, BinBuf bb, int nt) {
   if (!rebuilding(ctl)) return;
-  if (nt > 0 && p.omega_norm == 0.0) bb.tcell_overflow[1] = 1u;  // element lists kept
+  if (nt > 0) bb.tcell_overflow[1] = 1u;  // element lists kept
   ctl->phase ^= 1u;
   ctl->lphase ^= 1u;
   ctl->rebuilds += 1;
@@ -538,7 +575,7 @@ void launch_rebuild(cudaStream_t st, Ctl* ctl, const Params& p, StateBufs sb, Li
                     BinBuf bb, MeshDev mesh) {
   const unsigned nb = blocks_for(p.n, kThreads);
   const unsigned gcells = (unsigned)std::min<int64_t>(blocks_for(p.ncells, kThreads), 152 * 16);
-  k_rebuild_prep<<<1, 1, 0, st>>>(ctl);
+  k_rebuild_prep<<<1, 1, 0, st>>>(ctl, p);
   k_clear<<<gcells, kThreads, 0, st>>>(ctl, bb.cell_count, p.ncells + 1);
   k_bin_count<<<nb, kThreads, 0, st>>>(ctl, p, sb, bb, L);
   launch_scan(st, ctl, bb.cell_count, bb.cell_start, p.ncells + 1, bb.block_sums);

@@ -141,7 +141,23 @@ k_spawn(Ctl* ctl, Params p, StateBufs sb, BinBuf bb, MeshDev mesh) {
     for (uint32_t k = lane; k < kept && !ov; k += 32)
       ov = overlaps(cx, cy, cz, r, Sphere{kx[k], ky[k], kz[k], kr[k]});
     if (mesh.nt > 0) {
-      const uint32_t cell = cell_index(p, cc);
+      // the element lists are in the mesh's frame: the centre turned back by
+      // the rotation of this step selects the list (the test itself is made
+      // against the elements at their current pose)
+      int3 cm = cc;
+      if (p.omega_norm > 0.0) {
+        const double th = p.omega_norm * ((double)ctl->step * p.dt);
+        const double co = cos(th), si = sin(th);
+        const V3<double> ax = (1.0 / p.omega_norm) *
+                              mk(p.mesh_omega[0], p.mesh_omega[1], p.mesh_omega[2]);
+        const V3<double> cen = mk(p.mesh_center[0], p.mesh_center[1], p.mesh_center[2]);
+        const V3<double> rr = mk(cx, cy, cz) - cen;
+        const V3<double> qm =
+            cen + (co * rr - si * cross(ax, rr) + (dot(ax, rr) * (1.0 - co)) * ax);
+        cm = cell_coords(p, (float)(qm.x - p.origin[0]), (float)(qm.y - p.origin[1]),
+                         (float)(qm.z - p.origin[2]));
+      }
+      const uint32_t cell = cell_index(p, cm);
       const uint32_t e = min(bb.tcell_start[cell + 1], bb.tcap);
       for (uint32_t i = bb.tcell_start[cell] + lane; i < e && !ov; i += 32) {
         const uint32_t k = bb.tcell_tri[i];
