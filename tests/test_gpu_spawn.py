@@ -19,9 +19,10 @@ def dem():
     return d
 
 
-def spawn_scene(n_init=40, n_max=500, attempts=40, every=10, seed=21):
+def spawn_scene(n_init=40, n_max=500, attempts=40, every=10, seed=21, spin=0.0):
     """A floor plate (radius 0.2 mm), a few resting spheres, and a spawn box
-    above them: spawned spheres fall onto the floor and each other."""
+    above them: spawned spheres fall onto the floor and each other.  spin:
+    the plate turns about the vertical axis at this rate (rad/s)."""
     rng = np.random.default_rng(seed)
     V = np.array([[-0.015, -0.015, 0], [0.015, -0.015, 0], [0.015, 0.015, 0],
                   [-0.015, 0.015, 0]], dtype=np.float64)
@@ -34,7 +35,7 @@ def spawn_scene(n_init=40, n_max=500, attempts=40, every=10, seed=21):
     sp = dict(n_max=n_max, lo=(-0.009, -0.009, 0.0035), hi=(0.009, 0.009, 0.007),
               r_min=0.9e-3, r_max=1.1e-3, v0=(0.0, 0.0, -1.0), w0=(0.0, 0.0, 5.0),
               attempts=attempts, every=every, seed=seed)
-    p = scenes.base_params()
+    p = scenes.base_params(mesh_omega=(0.0, 0.0, spin), mesh_center=(0.0, 0.0, 0.0))
     return dict(params=p, R=R, x=x, v=None, w=None, q=None, verts=V, tris=None,
                 tri_radius=None, elems=E, elem_radius=np.array([0.2e-3]), spawn=sp)
 
@@ -45,9 +46,12 @@ def oracle_of(oracle_mod, s):
                                   tri_radius=rad, spawn=s["spawn"])
 
 
+@pytest.mark.parametrize("spin", [0.0, 20.0], ids=["still", "turning"])
 @pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
-def test_spawning_matches_oracle(dem, oracle_mod, precision):
-    s = spawn_scene()
+def test_spawning_matches_oracle(dem, oracle_mod, precision, spin):
+    # turning: the floor plate spins in its plane, so its element list is
+    # looked up in the plate's frame by the list build and by the spawn test
+    s = spawn_scene(spin=spin)
     sc = dem.Scene.from_dict(s, precision=precision, record_forces=True)
     oc = oracle_of(oracle_mod, s)
     # DEM_MIXED: 300 steps, the impacts of spawned spheres at 1 m/s amplify
