@@ -587,10 +587,12 @@ struct Mixed64Policy {
     return true;
   }
 
-  // The canonical pair (i, j): offset, distance and overlap in FP64 (the
-  // overlap is a small difference of two millimetre lengths), then rounded;
-  // everything after that in FP32.  Velocity and spin differences are formed
-  // in FP64 before rounding, so they keep their relative accuracy.
+  // The canonical pair (i, j): the offset and S^2 - d^2 = (S - d)(S + d) in
+  // FP64 (the overlap is a small difference of two millimetre lengths; the
+  // product form keeps it without a double-precision root), then the root and
+  // the overlap (S^2 - d^2) / (S + d) in FP32, and everything after that in
+  // FP32.  Velocity and spin differences are formed in FP64 before rounding,
+  // so they keep their relative accuracy.
   static __device__ __forceinline__ bool pair_law(const Params& p, const D4& Pi, const D4& Pj,
                                                   const D4& Vi, const D4& Vj, const D4& Wi,
                                                   const D4& Wj, const Aux& Ai, const Aux& Aj,
@@ -599,12 +601,12 @@ struct Mixed64Policy {
     const double dx = Pi.x - Pj.x, dy = Pi.y - Pj.y, dz = Pi.z - Pj.z;
     const double d2 = dx * dx + dy * dy + dz * dz;
     const double S = Pi.w + Pj.w;
-    if (d2 > S * S * (1.0 + 1e-10)) return false;
-    const double dist = sqrt(d2);
-    const double deltad = S - dist;
-    if (!(deltad >= 0.0) || !(dist > 0.0)) return false;
-    const float delta = (float)deltad;
-    const float idist = 1.f / (float)dist;
+    const double num = S * S - d2;
+    if (!(num >= 0.0)) return false;  // apart
+    const float dist = sqrtf((float)d2);
+    if (!(dist > 0.f)) return false;
+    const float delta = (float)num / ((float)S + dist);
+    const float idist = 1.f / dist;
     const V3<float> nh = mk((float)dx * idist, (float)dy * idist, (float)dz * idist);
     LawConst<float> cpp{p.f_Es_pp, p.f_Gs_pp, p.f_beta, p.f_mu_s, p.f_mu_r, p.f_mu_t, p.f_dt,
                         p.f_cs_cn_pp};
