@@ -66,3 +66,11 @@ def test_reference_arm_prints_only_on_rank_zero():
     line = json.loads(r.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["value"] > 0
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_sphere_count_names_the_workload_size():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.sphere_count(1_000_000) == "1M"
+    assert bench.sphere_count(400_000) == "400k"
+    assert bench.sphere_count(12_345) == "12345"

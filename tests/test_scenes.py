@@ -60,3 +60,25 @@ def test_generators_are_seeded():
     b = scenes.box_scene(n=50, seed=9)
     np.testing.assert_array_equal(a["x"], b["x"])
     np.testing.assert_array_equal(a["R"], b["R"])
+
+
+def test_repose_scene_knobs():
+    # the sensitivity knobs change only what they name: the time step, the
+    # plate gap, the spawn height and the grains' starting speed
+    base = scenes.repose_scene(n=20_000)
+    assert base["gap"] == pytest.approx(11 * 2e-3)
+    assert base["params"]["dt"] == pytest.approx(scenes.eq_dt(1e-3, 1000.0, 0.3, 1e6) / 10)
+    fine = scenes.repose_scene(n=20_000, dt_div=20)
+    assert fine["params"]["dt"] == pytest.approx(0.5 * base["params"]["dt"])
+    assert fine["z_spawn"] == base["z_spawn"] and fine["gap"] == base["gap"]
+    wide = scenes.repose_scene(n=20_000, gap_diameters=15)
+    assert wide["gap"] == pytest.approx(15 * 2e-3)
+    # a wider gap holds the same grains in a lower heap, so the stream starts lower
+    assert wide["z_spawn"] < base["z_spawn"]
+    low = scenes.repose_scene(n=20_000, spawn_angle=45.0)
+    assert low["z_spawn"] < base["z_spawn"] and low["params"]["dt"] == base["params"]["dt"]
+    # the spawn box stays above the heap of the named angle
+    area = 20_000 * (math.pi / 6.0) * (2e-3) ** 3 / (0.6 * low["gap"])
+    assert low["spawn"]["lo"][2] > math.sqrt(area * math.tan(math.radians(45.0)))
+    rest = scenes.repose_scene(n=20_000, v0=0.0)
+    assert rest["spawn"]["v0"] == (0.0, 0.0, 0.0) and rest["z_spawn"] == base["z_spawn"]
